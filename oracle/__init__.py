@@ -1,0 +1,172 @@
+"""CPU oracle for the subset-median k-d tree build.
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package. The CUDA library never imports it and the two share no code.
+
+The arithmetic lives in ``kdt_oracle.c`` (plain C, single-threaded); this
+module compiles it with gcc and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kdt_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "libkdt_oracle.so")
+
+KEY_CYCLIC = 0
+KEY_WIDEST_SPREAD = 1
+SUBSET_MOD = 0
+SUBSET_CONTIGUOUS = 1
+SUBSET_EXPLICIT = 2
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NAN_INPUT", 3: "OOM", 7: "LEVEL_CAP"}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status: int):
+        super().__init__(f"oracle status {status} ({STATUS.get(status, '?')})")
+        self.status = status
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("d", ctypes.c_int32),
+        ("subset_mode", ctypes.c_int32),
+        ("r", ctypes.c_int32),
+        ("sid8", ctypes.c_void_p),
+        ("sid16", ctypes.c_void_p),
+        ("depth", ctypes.c_int32),
+        ("leaf_size", ctypes.c_int32),
+        ("max_levels", ctypes.c_int32),
+        ("key_rule", ctypes.c_int32),
+    ]
+
+
+def build_library(force: bool = False) -> str:
+    """Compile kdt_oracle.c into a shared library (gcc, portable flags)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                   os.path.getmtime(os.path.join(_HERE, "kdt_oracle.h")))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra",
+                           "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build_library())
+        lib.kdto_key.restype = ctypes.c_uint32
+        lib.kdto_key.argtypes = [ctypes.c_float]
+        lib.kdto_key_value.restype = ctypes.c_float
+        lib.kdto_key_value.argtypes = [ctypes.c_uint32]
+        lib.kdto_build.restype = ctypes.c_int
+        lib.kdto_build.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Params), ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_int32)]
+        lib.kdto_split_cell.restype = ctypes.c_int
+        lib.kdto_split_cell.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Params), ctypes.c_void_p,
+                                        ctypes.c_int64, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_uint32),
+                                        ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_int64)]
+        _lib = lib
+    return _lib
+
+
+def key(x: float) -> int:
+    return int(_load().kdto_key(ctypes.c_float(x)))
+
+
+def key_value(k: int) -> float:
+    return float(_load().kdto_key_value(ctypes.c_uint32(k)))
+
+
+@dataclass
+class Tree:
+    perm: np.ndarray          # uint32 [n]
+    split_vals: np.ndarray    # float32 [2^L - 1]
+    split_dims: np.ndarray    # int8 [2^L - 1]
+    node_offsets: np.ndarray  # int64 [2^L + 1]
+    levels: int
+
+
+def _params(points: np.ndarray, r: int, subset_mode: int, sid, depth: int, leaf_size: int,
+            max_levels: int, key_rule: int):
+    d, n = points.shape
+    p = _Params()
+    p.n, p.d, p.subset_mode, p.r = n, d, subset_mode, r
+    p.sid8 = p.sid16 = None
+    keep = []
+    if sid is not None:
+        sid = np.ascontiguousarray(sid)
+        keep.append(sid)
+        if sid.dtype == np.uint8:
+            p.sid8 = sid.ctypes.data
+        elif sid.dtype == np.uint16:
+            p.sid16 = sid.ctypes.data
+        else:
+            raise TypeError("subset ids must be uint8 or uint16")
+    p.depth, p.leaf_size, p.max_levels, p.key_rule = depth, leaf_size, max_levels, key_rule
+    return p, keep
+
+
+def build_tree(points: np.ndarray, *, r: int = 1, subset_mode: int = SUBSET_MOD, sid=None,
+               depth: int = 0, leaf_size: int = 1, max_levels: int = 20,
+               key_rule: int = KEY_CYCLIC) -> Tree:
+    """Build with the plain CPU reference. points: float32 [d, n] (SoA)."""
+    points = np.ascontiguousarray(points, dtype=np.float32)
+    if points.ndim != 2:
+        raise ValueError("points must be [d, n]")
+    d, n = points.shape
+    p, keep = _params(points, r, subset_mode, sid, depth, leaf_size, max_levels, key_rule)
+    cap = depth if depth > 0 else max_levels
+    cap = max(0, min(cap, 30))
+    perm = np.zeros(max(n, 1), np.uint32)
+    vals = np.zeros(max((1 << cap) - 1, 1), np.float32)
+    dims = np.zeros(max((1 << cap) - 1, 1), np.int8)
+    offs = np.zeros((1 << cap) + 1, np.int64)
+    levels = ctypes.c_int32(0)
+    st = _load().kdto_build(points.ctypes.data, ctypes.byref(p), perm.ctypes.data, vals.ctypes.data,
+                            dims.ctypes.data, offs.ctypes.data, ctypes.byref(levels))
+    del keep
+    if st != 0:
+        raise OracleError(st)
+    L = levels.value
+    m = (1 << L) - 1
+    return Tree(perm[:n].copy(), vals[:m].copy(), dims[:m].copy(), offs[:(1 << L) + 1].copy(), L)
+
+
+def split_cell(points: np.ndarray, idx: np.ndarray, level: int, *, r: int = 1,
+               subset_mode: int = SUBSET_MOD, sid=None, key_rule: int = KEY_CYCLIC):
+    """Split of one cell whose points have original indices ``idx``.
+
+    Returns (dim, key, value, left_count)."""
+    points = np.ascontiguousarray(points, dtype=np.float32)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    p, keep = _params(points, r, subset_mode, sid, 1, 1, 1, key_rule)
+    dim, k, v, left = ctypes.c_int32(), ctypes.c_uint32(), ctypes.c_float(), ctypes.c_int64()
+    st = _load().kdto_split_cell(points.ctypes.data, ctypes.byref(p), idx.ctypes.data,
+                                 idx.size, level, ctypes.byref(dim), ctypes.byref(k),
+                                 ctypes.byref(v), ctypes.byref(left))
+    del keep
+    if st != 0:
+        raise OracleError(st)
+    return dim.value, k.value, v.value, left.value
