@@ -1,0 +1,151 @@
+/*
+ * kdt.h -- C ABI of the GB300 (sm_103a) level-by-level k-d tree build with
+ * subset-median splits.
+ *
+ * Paper: A. Chakravorty, W. S. Cleveland, P. J. Wolfe, "Scalable k-d trees
+ * for distributed data" (arXiv 2201.08288).
+ *
+ * What a build computes (all integer / compare arithmetic, bit-exact):
+ *   - The canonical k-d tree structure of Sec. 1 and Sec. 2: level l (0-based)
+ *     splits each of its 2^l cells along a key coordinate; a tree of depth D
+ *     has 2^D - 1 split statistics in level order (Sec. 2, last paragraph;
+ *     children of heap node h are 2h+1 and 2h+2).
+ *   - Key coordinate: cycled x, y, z, ... by level (Sec. 1), or per cell the
+ *     coordinate of widest dispersion (Sec. 1, Friedman rule), read as the
+ *     range (double)max - (double)min of the cell's points; lowest index wins
+ *     ties.
+ *   - The index set is partitioned into r subsets (Sec. 3.2, additivity of the
+ *     statistics over any partition; App. C.2, the user-supplied partition
+ *     I_1..I_R). For every (cell, subset) the build takes the lower median of
+ *     the subset's keys in the cell (0-based rank (w-1)/2); the cell's split is
+ *     the count-weighted lower median of those medians: the smallest subset
+ *     median m such that the subsets whose median is <= m hold at least half of
+ *     the cell's points. (The paper combines additive Fourier moments instead,
+ *     Sec. 3.2 Eq. (1)-(2); this combine rule is the library's.)
+ *   - Points with key <= split go left ("ties to the left"), others right; the
+ *     partition is stable, so every leaf lists its points in increasing
+ *     original index. Keys compare as floats with -0.0 < +0.0.
+ *   - Empty cells (depth mode) and terminal cells (leaf mode) record split
+ *     dim -1 and value +inf and pass all their points to the left child. In
+ *     leaf mode a cell is terminal when it holds <= leaf_size points or when
+ *     its last s splits each left the right child empty (s = d for cyclic
+ *     keys, s = 1 for widest spread); L is the first level whose cells are all
+ *     terminal.
+ *
+ * Conventions: every pointer argument marked "device" is a CUDA device
+ * pointer owned by the caller; the library never frees it. Calls are issued
+ * on `stream` (a cudaStream_t; NULL = legacy default stream) and return after
+ * the build has finished (the status needs one synchronisation). No function
+ * allocates device memory except where stated.
+ */
+#ifndef KDT_H
+#define KDT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum kdt_status {
+  KDT_OK = 0,
+  KDT_ERR_INVALID_ARG = 1, /* a parameter is out of range or a pointer is missing      */
+  KDT_ERR_NAN_INPUT = 2,   /* a coordinate is NaN; outputs are undefined              */
+  KDT_ERR_OOM = 3,         /* the library could not allocate memory it needed          */
+  KDT_ERR_CUDA = 4,        /* a CUDA runtime call failed                              */
+  KDT_ERR_CAPACITY = 5,    /* a caller-provided buffer is too small                   */
+  KDT_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                           */
+  KDT_ERR_LEVEL_CAP = 7,   /* leaf mode needs more than max_levels levels             */
+  KDT_ERR_BUSY = 8,        /* the server cannot take the request now                  */
+  KDT_ERR_NOT_FOUND = 9    /* unknown server ticket                                   */
+} kdt_status;
+
+typedef enum kdt_key_rule { KDT_KEY_CYCLIC = 0, KDT_KEY_WIDEST_SPREAD = 1 } kdt_key_rule;
+
+/* How points map to the r subsets (Sec. 3.2 / App. C.2 partition of I). */
+typedef enum kdt_subset_mode {
+  KDT_SUBSET_MOD = 0,        /* subset(i) = i mod r                                 */
+  KDT_SUBSET_CONTIGUOUS = 1, /* subset(i) = floor(i * r / n), 64-bit arithmetic     */
+  KDT_SUBSET_EXPLICIT = 2    /* subset(i) = subset_id8[i] or subset_id16[i] (< r)   */
+} kdt_subset_mode;
+
+/* Largest accepted depth / max_levels. */
+#define KDT_MAX_LEVELS 30
+/* Largest accepted number of subsets on the CUDA path. */
+#define KDT_MAX_SUBSETS 4096
+/* Largest accepted dimension. */
+#define KDT_MAX_DIMS 64
+
+typedef struct kdt_params {
+  int64_t n;                     /* points, 0 <= n <= 2^32 - 1                          */
+  int32_t d;                     /* coordinates per point, 1..64                        */
+  int32_t subset_mode;           /* kdt_subset_mode                                     */
+  int32_t r;                     /* subsets, 1..4096                                    */
+  int32_t key_rule;              /* kdt_key_rule                                        */
+  const uint8_t *subset_id8;     /* explicit mode: device, [n], exactly one of the two  */
+  const uint16_t *subset_id16;   /*   id arrays non-NULL; every id < r                  */
+  int32_t depth;                 /* > 0: fixed depth (2^depth leaves); 0: leaf mode     */
+  int32_t leaf_size;             /* leaf mode: cells with <= leaf_size points stop (>= 1) */
+  int32_t max_levels;            /* leaf mode: output capacity, 2^max_levels leaves     */
+  int32_t reserved;              /* must be 0                                           */
+} kdt_params;
+
+/*
+ * Bytes of device workspace kdt_build needs for these parameters on the
+ * current device. The workspace holds two ping-pong copies of the points,
+ * permutation and subset ids, a key scratch array and per-level tables.
+ * Errors: KDT_ERR_INVALID_ARG.
+ */
+kdt_status kdt_workspace_size(const kdt_params *p, size_t *bytes);
+
+/*
+ * Build one tree.
+ *   points           device, float32 SoA [d][n]: points[j*n + i] = coordinate j
+ *                    of point i. Read only.
+ *   workspace        device, >= kdt_workspace_size bytes, 256-byte aligned; or
+ *                    NULL, in which case the library allocates it (cudaMalloc)
+ *                    and frees it before returning.
+ *   out_perm         device [n]: original index of the point at each position of
+ *                    the final order (leaves in order, increasing index inside).
+ *   out_split_vals   device [2^L - 1]: split value of each node in level order
+ *                    (bit-identical to a coordinate of the node's points).
+ *   out_split_dims   device [2^L - 1]: split coordinate, -1 for sentinels.
+ *   out_node_offsets device [2^L + 1]: leaf k holds out_perm[offs[k]..offs[k+1]).
+ *   out_levels       host: L, the number of split levels built (depth, or the
+ *                    leaf-mode result). Capacity: outputs must hold
+ *                    2^depth (depth mode) or 2^max_levels (leaf mode) leaves.
+ * Errors: KDT_ERR_INVALID_ARG, KDT_ERR_NAN_INPUT, KDT_ERR_LEVEL_CAP,
+ *         KDT_ERR_CAPACITY (workspace too small), KDT_ERR_OOM, KDT_ERR_CUDA.
+ */
+kdt_status kdt_build(const float *points, const kdt_params *p, void *workspace,
+                     size_t workspace_bytes, uint32_t *out_perm, float *out_split_vals,
+                     int8_t *out_split_dims, int64_t *out_node_offsets, int32_t *out_levels,
+                     void *stream);
+
+/*
+ * Same build with HOST buffers: points, the explicit subset ids in p and all
+ * outputs are host pointers (pinned memory gives full copy bandwidth). The
+ * inputs are copied to the device, the tree is built, the outputs are copied
+ * back, all on `stream`, before returning.
+ *   workspace  device, >= kdt_workspace_size_host bytes (or NULL: allocated
+ *              and freed by the call).
+ * Errors: as kdt_build.
+ */
+kdt_status kdt_workspace_size_host(const kdt_params *p, size_t *bytes);
+kdt_status kdt_build_host(const float *points_host, const kdt_params *p, void *workspace,
+                          size_t workspace_bytes, uint32_t *out_perm_host,
+                          float *out_split_vals_host, int8_t *out_split_dims_host,
+                          int64_t *out_node_offsets_host, int32_t *out_levels, void *stream);
+
+/* Largest cell (points) the in-shared-memory subtree kernel takes for d
+ * coordinates; larger cells are split by the multi-CTA level pipeline. */
+int32_t kdt_subtree_capacity(int32_t d);
+
+/* Static description of a status code. */
+const char *kdt_status_str(kdt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KDT_H */

@@ -1,0 +1,283 @@
+// kdt_internal.cuh -- device-side types and helpers of the CUDA k-d tree build.
+//
+// The build follows the level structure of the canonical k-d tree (paper,
+// Sec. 1 and Sec. 2): level l splits each of its cells along one key
+// coordinate, children of heap node h are 2h+1 and 2h+2. Each cell's split is
+// combined from per-subset medians (the subsets of Sec. 3.2 / App. C.2); the
+// per-subset statistic is the lower median and the combination is the
+// count-weighted lower median of those medians.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kdt {
+
+// ----------------------------------------------------------------- limits
+
+constexpr int kMaxDims = 64;          // d <= 64
+constexpr int kMaxSubsets = 4096;     // r <= 4096 on the CUDA path
+constexpr int kMaxLevels = 30;        // depth / max_levels <= 30
+constexpr int kTile = 2048;           // points per tile of the multi-CTA pipeline
+constexpr int kTileThreads = 256;     // threads of the tile kernels
+constexpr int kSelSmallMax = 4096;    // segments up to this size: one warp per segment
+constexpr int kSubtreeThreads = 512;  // threads of the in-shared-memory subtree kernel
+constexpr int kSubtreeBins = 4096;    // (cell, subset) bins per batch in the subtree kernel
+constexpr int kSubtreeWarps = kSubtreeThreads / 32;
+
+// status codes (mirror include/kdt.h)
+enum : int32_t {
+  ST_OK = 0,
+  ST_INVALID_ARG = 1,
+  ST_NAN_INPUT = 2,
+  ST_OOM = 3,
+  ST_CUDA = 4,
+  ST_CAPACITY = 5,
+  ST_TIMEOUT = 6,
+  ST_LEVEL_CAP = 7,
+};
+
+enum : int32_t { KEY_CYCLIC = 0, KEY_WIDEST = 1 };
+enum : int32_t { SUB_MOD = 0, SUB_CONTIG = 1, SUB_EXPLICIT = 2 };
+
+// --------------------------------------------------------- data structures
+
+// Everything a kernel needs to know about one tree. Level l reads its points
+// from src(l) and the multi-CTA partition writes them to dst(l):
+//   src(0) = caller input (perm = identity), src(l>0) = buf[(l-1)&1],
+//   dst(l) = buf[l&1].
+struct TreeDev {
+  int64_t n;
+  int32_t d, r, subset_mode, key_rule;
+  int32_t depth;       // > 0 depth mode
+  int32_t leaf_size;   // leaf mode
+  int32_t max_levels;  // leaf mode level cap
+  int32_t stall_limit; // d (cyclic) or 1 (widest)
+  int32_t sid_bytes;   // explicit mode: 1 or 2
+  int32_t small_max;   // cells up to this size finish in the subtree kernel
+  int32_t pad0;
+  const float* x_in;
+  const void* sid_in;
+  float* xbuf[2];
+  uint32_t* pbuf[2];
+  void* sbuf[2];
+  uint32_t* keys;        // [n] per-level scratch (keys grouped by (cell, subset))
+  uint32_t* out_perm;
+  float* out_vals;
+  int8_t* out_dims;
+  int64_t* out_offs;
+  struct TermRec* terms; // terminal cells
+  uint32_t term_cap;
+  uint32_t pad1;
+  uint32_t* term_count;
+  int32_t* status;
+  int32_t* levels;       // L (max terminal level in leaf mode)
+};
+
+// A cell of the tree: a contiguous position range [begin, begin+count) of its
+// tree's current order.
+struct Cell {
+  uint32_t begin;
+  uint32_t count;
+  uint32_t heap;
+  int32_t tree;
+  int16_t level;
+  int16_t stall;  // consecutive splits on this path that left the right child empty
+};
+
+// A terminal cell (leaf of the real tree); finalize turns these into offsets
+// and sentinels below them.
+struct TermRec {
+  uint32_t begin;
+  uint32_t count;
+  uint32_t heap;
+  int32_t level;
+};
+
+// Per-step arrays of the multi-CTA pipeline (one entry per big cell / tile /
+// (cell, subset) segment).
+struct StepDev {
+  const Cell* cells;      // big cells of this step
+  uint32_t ncells;
+  uint32_t pad;
+  uint32_t* tile_base;    // [ncells+1] first tile of each cell (exclusive scan)
+  uint32_t* seg_base;     // [ncells+1] first segment of each cell
+  uint2* tiles;           // [ntiles] (cell, offset within cell)
+  uint32_t* ntiles_total; // device word
+  uint32_t* kdim;         // [ncells] key coordinate
+  uint32_t* mkey;         // [ncells] split key
+  uint32_t* lcount;       // [ncells] left child size
+  uint32_t* tile_mm;      // [ntiles][kMaxDims][2] per-tile min/max keys (widest)
+  uint32_t* seg_w;        // [nseg] points per (cell, subset)
+  uint32_t* seg_beg;      // [nseg] absolute scratch position
+  uint32_t* seg_cur;      // [nseg] fill cursor
+  uint32_t* seg_med;      // [nseg] lower median key
+  uint32_t* seg_cell;     // [nseg] owning cell
+  uint32_t* bigseg;       // [cap] segments larger than kSelSmallMax
+  uint32_t* bigseg_count; // device word
+  uint32_t* tile_left;    // [ntiles]
+  uint32_t* tile_loff;    // [ntiles]
+  Cell* next_big;         // children that stay in the multi-CTA pipeline
+  uint32_t* next_big_count;
+  Cell* small;            // children that finish in the subtree kernel
+  uint32_t* small_count;
+  uint32_t next_big_cap;
+  uint32_t small_cap;
+};
+
+// ------------------------------------------------------------- key transform
+
+// Order-preserving map float -> uint32: unsigned comparison of keys equals
+// the float order, with -0.0 below +0.0.
+__device__ __forceinline__ uint32_t ord_key(float x) {
+  uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_float(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k ^ 0x80000000u) : ~k;
+  return __uint_as_float(u);
+}
+
+__device__ __forceinline__ bool is_nan_bits(float x) {
+  return (__float_as_uint(x) & 0x7fffffffu) > 0x7f800000u;
+}
+
+// -------------------------------------------------------------- tree views
+
+__device__ __forceinline__ const float* src_cols(const TreeDev& t, int level) {
+  return level == 0 ? t.x_in : t.xbuf[(level - 1) & 1];
+}
+__device__ __forceinline__ const uint32_t* src_perm(const TreeDev& t, int level) {
+  return level == 0 ? nullptr : t.pbuf[(level - 1) & 1];
+}
+__device__ __forceinline__ const void* src_sid(const TreeDev& t, int level) {
+  return level == 0 ? t.sid_in : t.sbuf[(level - 1) & 1];
+}
+
+__device__ __forceinline__ void set_status(const TreeDev& t, int32_t code) {
+  atomicCAS(t.status, ST_OK, code);
+}
+
+// Subset of the point at position pos whose original index is orig. An
+// explicit id >= r is reported as an invalid argument and replaced by 0 so
+// that no table is indexed out of range.
+__device__ __forceinline__ uint32_t subset_of(const TreeDev& t, const void* sidcol, uint32_t orig,
+                                              int64_t pos) {
+  if (t.subset_mode == SUB_MOD) return orig % (uint32_t)t.r;
+  if (t.subset_mode == SUB_CONTIG)
+    return (uint32_t)(((uint64_t)orig * (uint64_t)t.r) / (uint64_t)t.n);
+  const uint32_t s = t.sid_bytes == 1 ? (uint32_t)((const uint8_t*)sidcol)[pos]
+                                      : (uint32_t)((const uint16_t*)sidcol)[pos];
+  if (s >= (uint32_t)t.r) {
+    set_status(t, ST_INVALID_ARG);
+    return 0;
+  }
+  return s;
+}
+
+// Terminal test for a cell about to be processed at `level` (reading R8 in
+// leaf mode; empty cells and the last level in depth mode).
+__device__ __forceinline__ bool is_terminal(const TreeDev& t, uint32_t count, int level, int stall) {
+  if (t.depth > 0) return count == 0 || level >= t.depth;
+  return count <= (uint32_t)t.leaf_size || stall >= t.stall_limit;
+}
+
+__device__ __forceinline__ void record_terminal(const TreeDev& t, uint32_t begin, uint32_t count,
+                                                uint32_t heap, int level) {
+  uint32_t slot = atomicAdd(t.term_count, 1u);
+  if (slot < t.term_cap) {
+    t.terms[slot] = TermRec{begin, count, heap, level};
+  } else {
+    set_status(t, ST_CAPACITY);
+  }
+  atomicMax(t.levels, level);
+}
+
+// ------------------------------------------------------------ warp helpers
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ uint32_t warp_min(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ uint32_t warp_max(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Given a 256-bin histogram in shared memory (counts or weights) and a
+// 0-based target rank, the whole warp finds the digit whose bin holds that
+// rank; returns the digit and, in *below, the total of the lower bins.
+__device__ __forceinline__ uint32_t warp_find_digit(const uint32_t* hist, uint32_t rank,
+                                                    uint32_t* below) {
+  const int lane = threadIdx.x & 31;
+  uint32_t local[8];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    local[i] = hist[lane * 8 + i];
+    s += local[i];
+  }
+  uint32_t incl = warp_incl_scan(s);
+  uint32_t excl = incl - s;
+  // the lane whose range [excl, incl) contains rank
+  unsigned ballot = __ballot_sync(0xffffffffu, rank >= excl && rank < incl);
+  int owner = ballot ? __ffs(ballot) - 1 : 31;
+  uint32_t digit = 0, b = 0;
+  if (lane == owner) {
+    uint32_t acc = excl;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (rank < acc + local[i]) {
+        digit = lane * 8 + i;
+        b = acc;
+        break;
+      }
+      acc += local[i];
+    }
+  }
+  digit = __shfl_sync(0xffffffffu, digit, owner);
+  *below = __shfl_sync(0xffffffffu, b, owner);
+  return digit;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive
+// prefix and writes the block total. `tmp` holds 33 words.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  uint32_t incl = warp_incl_scan(v);
+  if (lane == 31) tmp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < nwarps ? tmp[lane] : 0u;
+    uint32_t wi = warp_incl_scan(w);
+    if (lane < nwarps) tmp[lane] = wi - w;
+    if (lane == nwarps - 1) tmp[32] = wi;
+  }
+  __syncthreads();
+  uint32_t r = tmp[warp] + incl - v;
+  *total = tmp[32];
+  __syncthreads();
+  return r;
+}
+
+}  // namespace kdt

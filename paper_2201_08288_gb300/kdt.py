@@ -1,0 +1,219 @@
+"""Thin Python binding of the C ABI in include/kdt.h (ctypes).
+
+Only argument marshalling happens here: torch allocates device memory and
+provides the stream; every step of the build runs in the CUDA library
+(`_build/libkdt.so`). Importing works without a GPU; calling a build without
+the compiled library raises immediately (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libkdt.so")
+
+KDT_KEY_CYCLIC = 0
+KDT_KEY_WIDEST_SPREAD = 1
+KDT_SUBSET_MOD = 0
+KDT_SUBSET_CONTIGUOUS = 1
+KDT_SUBSET_EXPLICIT = 2
+KDT_MAX_LEVELS = 30
+KDT_MAX_SUBSETS = 4096
+
+STATUS_NAMES = {0: "KDT_OK", 1: "KDT_ERR_INVALID_ARG", 2: "KDT_ERR_NAN_INPUT", 3: "KDT_ERR_OOM",
+                4: "KDT_ERR_CUDA", 5: "KDT_ERR_CAPACITY", 6: "KDT_ERR_TIMEOUT", 7: "KDT_ERR_LEVEL_CAP",
+                8: "KDT_ERR_BUSY", 9: "KDT_ERR_NOT_FOUND"}
+
+# Every symbol include/kdt.h declares (checked by the CPU test suite).
+EXPORTED = ["kdt_workspace_size", "kdt_build", "kdt_workspace_size_host", "kdt_build_host",
+            "kdt_subtree_capacity", "kdt_status_str"]
+
+
+class KdtError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+class kdt_params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("d", ctypes.c_int32),
+        ("subset_mode", ctypes.c_int32),
+        ("r", ctypes.c_int32),
+        ("key_rule", ctypes.c_int32),
+        ("subset_id8", ctypes.c_void_p),
+        ("subset_id16", ctypes.c_void_p),
+        ("depth", ctypes.c_int32),
+        ("leaf_size", ctypes.c_int32),
+        ("max_levels", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libkdt.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library missing: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER(kdt_params)
+    vp, sz = ctypes.c_void_p, ctypes.c_size_t
+    lib.kdt_workspace_size.argtypes = [P, ctypes.POINTER(sz)]
+    lib.kdt_workspace_size.restype = ctypes.c_int
+    lib.kdt_workspace_size_host.argtypes = [P, ctypes.POINTER(sz)]
+    lib.kdt_workspace_size_host.restype = ctypes.c_int
+    lib.kdt_build.argtypes = [vp, P, vp, sz, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), vp]
+    lib.kdt_build.restype = ctypes.c_int
+    lib.kdt_build_host.argtypes = [vp, P, vp, sz, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), vp]
+    lib.kdt_build_host.restype = ctypes.c_int
+    lib.kdt_subtree_capacity.argtypes = [ctypes.c_int32]
+    lib.kdt_subtree_capacity.restype = ctypes.c_int32
+    lib.kdt_status_str.argtypes = [ctypes.c_int]
+    lib.kdt_status_str.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def make_params(n: int, d: int, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid_ptr: int = 0,
+                sid_bytes: int = 1, depth: int = 0, leaf_size: int = 1, max_levels: int = 20,
+                key_rule: int = KDT_KEY_CYCLIC) -> kdt_params:
+    p = kdt_params()
+    p.n, p.d, p.subset_mode, p.r, p.key_rule = n, d, subset_mode, r, key_rule
+    p.subset_id8 = sid_ptr if (sid_ptr and sid_bytes == 1) else None
+    p.subset_id16 = sid_ptr if (sid_ptr and sid_bytes == 2) else None
+    p.depth, p.leaf_size, p.max_levels, p.reserved = depth, leaf_size, max_levels, 0
+    return p
+
+
+def kdt_workspace_size(p: kdt_params) -> int:
+    out = ctypes.c_size_t(0)
+    st = load_library().kdt_workspace_size(ctypes.byref(p), ctypes.byref(out))
+    if st:
+        raise KdtError(st, "kdt_workspace_size")
+    return out.value
+
+
+def kdt_workspace_size_host(p: kdt_params) -> int:
+    out = ctypes.c_size_t(0)
+    st = load_library().kdt_workspace_size_host(ctypes.byref(p), ctypes.byref(out))
+    if st:
+        raise KdtError(st, "kdt_workspace_size_host")
+    return out.value
+
+
+def kdt_subtree_capacity(d: int) -> int:
+    return int(load_library().kdt_subtree_capacity(d))
+
+
+def kdt_status_str(st: int) -> str:
+    return load_library().kdt_status_str(st).decode()
+
+
+@dataclass
+class Tree:
+    perm: "object"
+    split_vals: "object"
+    split_dims: "object"
+    node_offsets: "object"
+    levels: int
+
+
+def _capacity(depth: int, max_levels: int) -> int:
+    return depth if depth > 0 else max_levels
+
+
+def _sid_info(sid):
+    if sid is None:
+        return 0, 1
+    import torch
+    if sid.dtype == torch.uint8:
+        return sid.data_ptr(), 1
+    if sid.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)):
+        return sid.data_ptr(), 2
+    raise TypeError("subset ids must be uint8 or 16-bit")
+
+
+def kdt_build(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None, depth: int = 0,
+              leaf_size: int = 1, max_levels: int = 20, key_rule: int = KDT_KEY_CYCLIC,
+              workspace=None, stream=None, outputs: Optional[Tree] = None) -> Tree:
+    """Build on the device. points: torch float32 CUDA tensor [d, n], contiguous.
+    sid: uint8 (or int16 holding uint16) CUDA tensor [n] for explicit subsets.
+    workspace: optional uint8 CUDA tensor of >= kdt_workspace_size bytes.
+    outputs: optional preallocated Tree of tensors (sized for the capacity)."""
+    import torch
+    if not (points.is_cuda and points.dtype == torch.float32 and points.is_contiguous() and points.dim() == 2):
+        raise ValueError("points must be a contiguous float32 CUDA tensor [d, n]")
+    d, n = points.shape
+    sid_ptr, sid_bytes = _sid_info(sid)
+    p = make_params(n, d, r=r, subset_mode=subset_mode, sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth,
+                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule)
+    lib = load_library()
+    cap = _capacity(depth, max_levels)
+    dev = points.device
+    if outputs is None:
+        outputs = Tree(torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+                       torch.empty(max((1 << cap) - 1, 1), dtype=torch.float32, device=dev),
+                       torch.empty(max((1 << cap) - 1, 1), dtype=torch.int8, device=dev),
+                       torch.empty((1 << cap) + 1, dtype=torch.int64, device=dev), 0)
+    ws_ptr, ws_bytes = 0, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    levels = ctypes.c_int32(0)
+    st = lib.kdt_build(points.data_ptr(), ctypes.byref(p), ws_ptr or None, ws_bytes,
+                       outputs.perm.data_ptr(), outputs.split_vals.data_ptr(), outputs.split_dims.data_ptr(),
+                       outputs.node_offsets.data_ptr(), ctypes.byref(levels), stream.cuda_stream)
+    if st:
+        raise KdtError(st, "kdt_build")
+    L = levels.value
+    m = (1 << L) - 1
+    return Tree(outputs.perm[:n], outputs.split_vals[:m], outputs.split_dims[:m],
+                outputs.node_offsets[:(1 << L) + 1], L)
+
+
+def kdt_build_host(points: np.ndarray, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None,
+                   depth: int = 0, leaf_size: int = 1, max_levels: int = 20, key_rule: int = KDT_KEY_CYCLIC,
+                   workspace=None, stream=None, outputs=None) -> Tree:
+    """Build from HOST arrays (numpy, ideally pinned): copies in, builds, copies
+    the outputs back into numpy arrays, all inside the library call."""
+    import torch
+    points = np.ascontiguousarray(points, dtype=np.float32)
+    d, n = points.shape
+    sid_ptr, sid_bytes = 0, 1
+    if sid is not None:
+        sid = np.ascontiguousarray(sid)
+        sid_ptr, sid_bytes = sid.ctypes.data, sid.dtype.itemsize
+    p = make_params(n, d, r=r, subset_mode=subset_mode, sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth,
+                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule)
+    cap = _capacity(depth, max_levels)
+    if outputs is None:
+        outputs = Tree(np.empty(max(n, 1), np.uint32), np.empty(max((1 << cap) - 1, 1), np.float32),
+                       np.empty(max((1 << cap) - 1, 1), np.int8), np.empty((1 << cap) + 1, np.int64), 0)
+    ws_ptr, ws_bytes = 0, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    levels = ctypes.c_int32(0)
+    st = load_library().kdt_build_host(points.ctypes.data, ctypes.byref(p), ws_ptr or None, ws_bytes,
+                                       outputs.perm.ctypes.data, outputs.split_vals.ctypes.data,
+                                       outputs.split_dims.ctypes.data, outputs.node_offsets.ctypes.data,
+                                       ctypes.byref(levels), stream.cuda_stream)
+    if st:
+        raise KdtError(st, "kdt_build_host")
+    L = levels.value
+    m = (1 << L) - 1
+    return Tree(outputs.perm[:n], outputs.split_vals[:m], outputs.split_dims[:m],
+                outputs.node_offsets[:(1 << L) + 1], L)
