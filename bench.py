@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the level-by-level k-d tree build (subset-median splits) on GB300.
+
+One step = one complete kdt_build of the workload's tree through the C ABI,
+on inputs already resident in HBM (they are larger than L2). Prints one JSON
+line on rank 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c2|c1]
+    python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+N > 1 runs under torchrun: every rank builds its own tree of the same shape
+(a different seed) with no exchange between ranks ("replicas"); the value is
+the points x levels of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "build points×levels/s"
+UNIT = "points*levels/s"
+
+
+def workload(name: str, rank: int):
+    from paper_2201_08288_gb300 import workloads as W
+    if name == "c3":
+        spec = W.config3()
+    elif name == "c2":
+        spec = W.config2()
+    elif name == "c1":
+        spec = W.config1()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    spec.seed += 1000 * rank
+    if spec.sid_seed is not None:
+        spec.sid_seed += 1000 * rank
+    kw = dict(r=spec.r, subset_mode=spec.subset_mode, depth=spec.depth, key_rule=spec.key_rule,
+              leaf_size=spec.leaf_size, max_levels=spec.max_levels)
+    return spec, kw
+
+
+def bytes_per_point(kernel: str, d: int, sid_bytes: int, subset_mode: int) -> float:
+    """Algorithmic bytes one launch moves per point it processes."""
+    sid_src = sid_bytes if subset_mode == 2 else 4  # explicit id column, else derived from perm
+    return {
+        "k_part_scatter": 2.0 * (4 * d + 4 + sid_bytes),   # read + write every column, perm, ids
+        "k_subtree": 4.0 * d + 4 + sid_bytes + 4,           # stage everything once, write perm once
+        "k_group": 4.0 + sid_src + 4,                       # key + id in, key out
+        "k_seg_count": float(sid_src),
+        "k_part_count": 4.0,
+        "k_select_small": 4.0,
+        "k_minmax": 4.0 * d,
+    }.get(kernel, 0.0)
+
+
+def model_bytes_per_point_level(d: int, sid_bytes: int, subset_mode: int) -> float:
+    """Bytes each level must move per point (SoA ping-pong model): key read for
+    the select, the subset id source, read+write of all columns and the
+    permutation, read+write of an explicit id column."""
+    s_sel = sid_bytes if subset_mode == 2 else 4
+    return 4 + s_sel + 8 * (d + 1) + 2 * (sid_bytes if subset_mode == 2 else 0)
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "0x1") or v == "1":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_gbs() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel: str, workload_name: str):
+    """DRAM bytes per point of `kernel` from the committed ncu summary, if the
+    kernel sources are unchanged since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(p))[f"{kernel}:{workload_name}"]
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for f in sorted(rec.get("sources", [])):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest() != rec.get("sha256"):
+        return None
+    return float(rec["dram_bytes_per_point"])
+
+
+def cpu_baseline(name: str, target_s: float = 12.0) -> dict:
+    """The oracle as it stands, single-threaded on a host core, on a bounded
+    sample of the same workload recipe (fewer points, depth reduced so the
+    leaves keep the same size)."""
+    import oracle
+    from paper_2201_08288_gb300 import workloads as W
+    spec, kw = workload(name, 0)
+    full_n, full_depth = spec.n, spec.depth
+    n_s = 1 << 16
+    while True:
+        depth_s = max(1, full_depth - int(round(np.log2(full_n / n_s))))
+        s = W.TreeSpec(spec.name, n_s, spec.d, spec.dist, spec.seed, spec.r, spec.subset_mode, spec.key_rule,
+                       depth=depth_s, sid_seed=spec.sid_seed)
+        pts, sid = s.points(), s.sids()
+        t0 = time.perf_counter()
+        t = oracle.build_tree(pts, r=s.r, subset_mode=s.subset_mode, sid=sid, depth=depth_s, key_rule=s.key_rule)
+        dt = time.perf_counter() - t0
+        if dt * 4 > target_s or n_s >= full_n:
+            return {"value": n_s * t.levels / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "host_cores": os.cpu_count(),
+                    "sample": f"n={n_s} depth={depth_s} of the {spec.name} recipe, one build, {dt:.2f} s"}
+        n_s *= 2
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    spec, _ = workload(args.workload, 0)
+    import oracle
+    from paper_2201_08288_gb300 import workloads as W
+    n_s = 1 << 18
+    depth_s = max(1, spec.depth - int(round(np.log2(spec.n / n_s))))
+    s = W.TreeSpec(spec.name, n_s, spec.d, spec.dist, spec.seed, spec.r, spec.subset_mode, spec.key_rule,
+                   depth=depth_s, sid_seed=spec.sid_seed)
+    pts, sid = s.points(), s.sids()
+    kw = dict(r=s.r, subset_mode=s.subset_mode, sid=sid, depth=depth_s, key_rule=s.key_rule)
+    for _ in range(args.warmup):
+        oracle.build_tree(pts, **kw)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        t = oracle.build_tree(pts, **kw)
+    dt = time.perf_counter() - t0
+    value = args.steps * n_s * t.levels / dt
+    sample = f"n={n_s} depth={depth_s} of the {spec.name} recipe per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": spec.name, "reference_sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_2201_08288_gb300 import build as cuda_build, kdt
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        cuda_build.build()
+    if dist:
+        dist.barrier()
+    kdt.load_library()
+
+    spec, kw = workload(args.workload, rank)
+    pts = spec.points_device(dev)
+    sid = spec.sids_device(dev)
+    sid_bytes = 0 if sid is None else sid.element_size()
+    p = kdt.make_params(spec.n, spec.d, sid_ptr=sid.data_ptr() if sid is not None else 0,
+                        sid_bytes=max(sid_bytes, 1), **kw)
+    ws = torch.empty(kdt.kdt_workspace_size(p), dtype=torch.uint8, device=dev)
+    out = None
+    stream = torch.cuda.current_stream(dev)
+
+    # preallocated outputs (sized for the capacity)
+    cap = spec.depth if spec.depth > 0 else spec.max_levels
+    out = kdt.Tree(torch.empty(spec.n, dtype=torch.int32, device=dev),
+                   torch.empty((1 << cap) - 1, dtype=torch.float32, device=dev),
+                   torch.empty((1 << cap) - 1, dtype=torch.int8, device=dev),
+                   torch.empty((1 << cap) + 1, dtype=torch.int64, device=dev), 0)
+
+    def build_once():
+        return kdt.kdt_build(pts, sid=sid, workspace=ws, outputs=out, stream=stream, **kw)
+
+    for _ in range(args.warmup):
+        tree = build_once()
+    torch.cuda.synchronize()
+    levels = tree.levels
+
+    clocks = Clocks(dev.index if dev.index is not None else 0)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = kdt.kdt_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        build_once()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = kdt.kdt_launch_count() - launches0
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = world * args.steps * spec.n * levels
+    value = units / (ms / 1e3)
+
+    # per-kernel device time of the same steps, from CUDA events recorded by the library
+    kdt.kdt_trace_read(reset=True)
+    kdt.kdt_trace_enable(True)
+    for _ in range(args.steps):
+        build_once()
+    torch.cuda.synchronize()
+    stats = kdt.kdt_trace_read(reset=True)
+    kdt.kdt_trace_enable(False)
+    dominant = max(stats.items(), key=lambda kv: kv[1][1])[0]
+    nl, tot_ms, pts_done = stats[dominant]
+    bpp = bytes_per_point(dominant, spec.d, sid_bytes, spec.subset_mode)
+    peak, peak_src = measured_peak_gbs()
+    achieved = (pts_done * bpp) / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else 0.0
+    traffic_pp = recorded_traffic(dominant, args.workload)
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": pts_done * bpp / max(nl, 1),
+                "launches": nl, "avg_launch_ms": tot_ms / max(nl, 1),
+                "traffic": (traffic_pp * pts_done / max(nl, 1)) if traffic_pp is not None else None,
+                "share_of_step": tot_ms / (ms / args.steps * args.steps) if ms > 0 else None}
+    kernel_table = {k: {"launches": v[0], "ms": round(v[1], 3), "points": v[2]} for k, v in stats.items()}
+    mb = model_bytes_per_point_level(spec.d, sid_bytes, spec.subset_mode)
+    build_model_gbs = spec.n * levels * mb / (ms / args.steps / 1e3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        host_pts = torch.empty(pts.shape, dtype=torch.float32, pin_memory=True)
+        host_pts.copy_(pts)
+        host_sid = None
+        if sid is not None:
+            host_sid = torch.empty(sid.shape, dtype=sid.dtype, pin_memory=True)
+            host_sid.copy_(sid)
+        hp = kdt.make_params(spec.n, spec.d, sid_ptr=1 if sid is not None else 0, sid_bytes=max(sid_bytes, 1),
+                             **kw)
+        ws_h = torch.empty(kdt.kdt_workspace_size_host(hp), dtype=torch.uint8, device=dev)
+        del ws
+        torch.cuda.empty_cache()
+        o_perm = torch.empty(spec.n, dtype=torch.int32, pin_memory=True)
+        o_vals = torch.empty((1 << cap) - 1, dtype=torch.float32, pin_memory=True)
+        o_dims = torch.empty((1 << cap) - 1, dtype=torch.int8, pin_memory=True)
+        o_offs = torch.empty((1 << cap) + 1, dtype=torch.int64, pin_memory=True)
+        houts = kdt.Tree(o_perm.numpy(), o_vals.numpy(), o_dims.numpy(), o_offs.numpy(), 0)
+        hsid = host_sid.numpy() if host_sid is not None else None
+        if hsid is not None and hsid.dtype == np.int16:
+            hsid = hsid.view(np.uint16)
+
+        def e2e_once():
+            return kdt.kdt_build_host(host_pts.numpy(), sid=hsid, workspace=ws_h, stream=stream,
+                                      outputs=houts, **kw)
+        for _ in range(args.warmup):
+            e2e_once()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ht = e2e_once()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_s = float(t.item())
+        nleaf = 1 << ht.levels
+        e2e = {"value": world * args.steps * spec.n * ht.levels / e_s, "unit": UNIT,
+               "h2d_bytes_per_step": spec.d * spec.n * 4 + spec.n * sid_bytes,
+               "d2h_bytes_per_step": spec.n * 4 + (nleaf - 1) * 5 + (nleaf + 1) * 8,
+               "ms_per_step": 1e3 * e_s / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": spec.name, "n": spec.n, "d": spec.d, "r": spec.r,
+                       "subset_mode": ["mod", "contiguous", "explicit"][spec.subset_mode],
+                       "key_rule": ["cyclic", "widest_spread"][spec.key_rule], "depth": spec.depth,
+                       "levels": levels, "parallelism": f"replicas{world}",
+                       "l2": f"inputs larger than L2 ({spec.d * spec.n * 4 / 1e9:.1f} GB per step)"},
+            "roofline": roofline,
+            "build_model_gbs": build_model_gbs, "build_model_frac": build_model_gbs / peak,
+            "model_bytes_per_point_level": mb,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "kernels": kernel_table,
+        }))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

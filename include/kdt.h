@@ -138,6 +138,26 @@ kdt_status kdt_build_host(const float *points_host, const kdt_params *p, void *w
                           float *out_split_vals_host, int8_t *out_split_dims_host,
                           int64_t *out_node_offsets_host, int32_t *out_levels, void *stream);
 
+/* ---- tracing ------------------------------------------------------------
+ * Every kernel launch of the library is counted. With tracing enabled, each
+ * launch is also bracketed by two CUDA events recorded on its stream;
+ * kdt_trace_read waits for them and reports, per kernel, the number of
+ * launches, their summed device time and the points they processed. */
+typedef struct kdt_kernel_stat {
+  const char *name;   /* kernel name (static string)                       */
+  uint64_t launches;  /* timed launches                                    */
+  double total_ms;    /* summed event-to-event device time                 */
+  uint64_t units;     /* points processed by those launches (0: not counted) */
+} kdt_kernel_stat;
+
+/* Turn per-launch event timing on (1) or off (0). Process-wide. */
+void kdt_trace_enable(int32_t on);
+/* Kernel launches issued by the library since the process started. */
+uint64_t kdt_launch_count(void);
+/* Fill up to max entries (out may be NULL); returns the number of kernels
+ * with data. Synchronises on the recorded events. reset != 0 clears totals. */
+int32_t kdt_trace_read(kdt_kernel_stat *out, int32_t max, int32_t reset);
+
 /* Largest cell (points) the in-shared-memory subtree kernel takes for d
  * coordinates; larger cells are split by the multi-CTA level pipeline. */
 int32_t kdt_subtree_capacity(int32_t d);

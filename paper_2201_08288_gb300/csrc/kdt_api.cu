@@ -32,13 +32,17 @@ struct Layout {
   size_t xbuf[2] = {0, 0}, pbuf[2] = {0, 0}, sbuf[2] = {0, 0}, keys = 0, terms = 0, tree = 0,
          words = 0;
   size_t big[2] = {0, 0}, small = 0, tile_base = 0, seg_base = 0, tiles = 0, tile_left = 0,
-         tile_loff = 0, tile_mm = 0, kdim = 0, mkey = 0, lcount = 0, seg_w = 0, seg_beg = 0,
+         tile_loff = 0, tile_mm = 0, child_mm = 0, kdim = 0, mkey = 0, lcount = 0, seg_w = 0, seg_beg = 0,
          seg_cur = 0, seg_med = 0, seg_cell = 0, bigseg = 0, slices = 0;
   size_t total = 0;
 };
 
 // Device words at Layout::words.
-enum Word { W_TERM = 0, W_STATUS, W_LEVELS, W_NTILES, W_BIGSEG, W_NEXTBIG, W_SMALL, W_HEAD, W_COUNT };
+enum Word {
+  W_TERM = 0, W_STATUS, W_LEVELS, W_NTILES, W_BIGSEG, W_HEAD,
+  W_NEXTBIG, W_SMALL, W_BIGPTS, W_SMALLPTS,  // read back together after each step
+  W_COUNT
+};
 
 kdt_status validate(const kdt_params* p) {
   if (!p) return KDT_ERR_INVALID_ARG;
@@ -110,7 +114,8 @@ Layout make_layout(const kdt_params& p) {
   L.tiles = take((size_t)L.max_tiles * sizeof(uint2));
   L.tile_left = take((size_t)L.max_tiles * 4);
   L.tile_loff = take((size_t)L.max_tiles * 4);
-  L.tile_mm = take(widest ? (size_t)L.max_tiles * kMaxDims * 2 * 4 : 0);
+  L.tile_mm = take(widest ? (size_t)L.max_tiles * 2 * kMaxDims * 2 * 4 : 0);
+  L.child_mm = take(widest ? (size_t)L.maxB * 2 * kMaxDims * 2 * 4 : 0);
   L.kdim = take((size_t)L.maxB * 4);
   L.mkey = take((size_t)L.maxB * 4);
   L.lcount = take((size_t)L.maxB * 4);
@@ -189,7 +194,7 @@ kdt_status build_device(const float* points, const kdt_params& p, uint8_t* ws, c
   LCell* slices = (LCell*)(ws + L.slices);
 
   // root
-  const Cell root{0u, (uint32_t)n, 0u, 0, 0, 0};
+  const Cell root{0u, (uint32_t)n, 0u, 0, 0, 0, -1};
   const bool root_terminal = p.depth > 0 ? (n == 0) : (n <= (uint64_t)p.leaf_size);
   uint32_t B = 0, small_total = 0, small_done = 0;
   if (root_terminal) {
@@ -216,6 +221,7 @@ kdt_status build_device(const float* points, const kdt_params& p, uint8_t* ws, c
   s.mkey = (uint32_t*)(ws + L.mkey);
   s.lcount = (uint32_t*)(ws + L.lcount);
   s.tile_mm = (uint32_t*)(ws + L.tile_mm);
+  s.child_mm = (uint32_t*)(ws + L.child_mm);
   s.seg_w = (uint32_t*)(ws + L.seg_w);
   s.seg_beg = (uint32_t*)(ws + L.seg_beg);
   s.seg_cur = (uint32_t*)(ws + L.seg_cur);
@@ -230,34 +236,45 @@ kdt_status build_device(const float* points, const kdt_params& p, uint8_t* ws, c
   s.small_count = words + W_SMALL;
   s.small_cap = L.cap_small;
   s.next_big_cap = L.maxB;
+  s.next_big_points = words + W_BIGPTS;
+  s.small_points = words + W_SMALLPTS;
 
   const bool widest = p.key_rule == KDT_KEY_WIDEST_SPREAD;
   int cur = 0;
+  int level = 0;
+  uint64_t big_points = B ? n : 0, small_points_done = 0;
+  uint64_t small_points_total = (!root_terminal && B == 0) ? n : 0;
   while (B > 0) {
-    if (B > L.maxB) return KDT_ERR_CAPACITY;
     s.cells = big[cur];
     s.ncells = B;
     s.next_big = big[cur ^ 1];
     KDT_CUDA_TRY(cudaMemsetAsync(s.next_big_count, 0, 4, st));
-    launch_big_step(d_tree, s, L.max_tiles, B * (uint32_t)p.r, L.bigseg_cap, widest, st);
+    KDT_CUDA_TRY(cudaMemsetAsync(s.next_big_points, 0, 4, st));
+    launch_big_step(d_tree, s, L.max_tiles, B * (uint32_t)p.r, L.bigseg_cap, widest && level == 0, widest,
+                    p.d, big_points, st);
     KDT_CUDA_TRY(cudaGetLastError());
-    uint32_t counts[2];
-    KDT_CUDA_TRY(cudaMemcpyAsync(counts, words + W_NEXTBIG, 8, cudaMemcpyDeviceToHost, st));
+    uint32_t counts[4];
+    KDT_CUDA_TRY(cudaMemcpyAsync(counts, words + W_NEXTBIG, 16, cudaMemcpyDeviceToHost, st));
     KDT_CUDA_TRY(cudaStreamSynchronize(st));
     small_total = std::min(counts[1], L.cap_small);
-    if (counts[0] > L.maxB) counts[0] = L.maxB;
+    small_points_total = counts[3];
     if (small_total > small_done) {
       launch_subtree(d_tree, small + small_done, small_total - small_done, words + W_HEAD, slices,
-                     L.slice_cells, std::min(L.grid_sub, small_total - small_done), st);
+                     L.slice_cells, std::min(L.grid_sub, small_total - small_done),
+                     small_points_total - small_points_done, st);
       KDT_CUDA_TRY(cudaGetLastError());
       small_done = small_total;
+      small_points_done = small_points_total;
     }
-    B = counts[0];
+    B = std::min(counts[0], L.maxB);
+    big_points = counts[2];
     cur ^= 1;
+    ++level;
   }
   if (small_total > small_done) {
     launch_subtree(d_tree, small + small_done, small_total - small_done, words + W_HEAD, slices,
-                   L.slice_cells, std::min(L.grid_sub, small_total - small_done), st);
+                   L.slice_cells, std::min(L.grid_sub, small_total - small_done),
+                   small_points_total - small_points_done, st);
     KDT_CUDA_TRY(cudaGetLastError());
   }
   uint32_t fin[3];

@@ -80,8 +80,9 @@ struct Cell {
   uint32_t count;
   uint32_t heap;
   int32_t tree;
-  int16_t level;
-  int16_t stall;  // consecutive splits on this path that left the right child empty
+  int8_t level;
+  int8_t stall;   // consecutive splits on this path that left the right child empty
+  int16_t dim;    // widest-spread key coordinate if already known, else -1
 };
 
 // A terminal cell (leaf of the real tree); finalize turns these into offsets
@@ -106,7 +107,9 @@ struct StepDev {
   uint32_t* kdim;         // [ncells] key coordinate
   uint32_t* mkey;         // [ncells] split key
   uint32_t* lcount;       // [ncells] left child size
-  uint32_t* tile_mm;      // [ntiles][kMaxDims][2] per-tile min/max keys (widest)
+  uint32_t* tile_mm;      // [ntiles][2][kMaxDims][2] per-tile min/max keys (widest): at the
+                          // root per tile of the cell itself, after the scatter per child side
+  uint32_t* child_mm;     // [ncells][2][kMaxDims][2] per-child min/max keys (widest)
   uint32_t* seg_w;        // [nseg] points per (cell, subset)
   uint32_t* seg_beg;      // [nseg] absolute scratch position
   uint32_t* seg_cur;      // [nseg] fill cursor
@@ -122,6 +125,8 @@ struct StepDev {
   uint32_t* small_count;
   uint32_t next_big_cap;
   uint32_t small_cap;
+  uint32_t* next_big_points;  // points in next_big (for bandwidth accounting)
+  uint32_t* small_points;     // points appended to small
 };
 
 // ------------------------------------------------------------- key transform

@@ -8,43 +8,59 @@
 
 namespace kdt {
 
-// Per-level local cell of the subtree kernel (kept in a per-CTA slice of
-// global memory).
+// Per-level local cell of the subtree kernel (shared memory while a level has
+// at most kSubtreeSmemCells live cells, else a per-CTA slice of global memory).
 struct LCell {
-  uint32_t begin;   // local position
-  uint32_t count;
   uint32_t heap;
-  int32_t stall;
-  uint32_t dim;
-  uint32_t mkey;
-  uint32_t lcount;
-  uint32_t pad;
+  uint32_t mkey;    // split key
+  uint16_t begin;   // local position
+  uint16_t count;
+  uint16_t lcount;  // left child size
+  uint8_t dim;      // key coordinate
+  uint8_t stall;    // consecutive splits that left the right child empty
 };
+static_assert(sizeof(LCell) == 16, "LCell is 16 bytes");
 
 // Shared-memory budget of the subtree kernel.
-constexpr size_t kSubtreeSmemBytes = 231424;        // dynamic part
+constexpr size_t kSubtreeSmemBytes = 231424;  // dynamic part
 constexpr int kSubtreeBigBinCap = 1024;
+constexpr int kSubtreeSmemCells = 512;
 constexpr size_t kSubtreeFixedBytes =
-    (size_t)(kSubtreeBins + 1) * 4 + (size_t)kSubtreeBins * 4 + (size_t)kSubtreeWarps * 256 * 4 +
-    (size_t)kSubtreeBigBinCap * 2;
+    16400 /* bins */ + (size_t)kSubtreeBins * 4 /* medians */ + (size_t)kSubtreeWarps * 256 * 4 +
+    (size_t)kSubtreeBigBinCap * 2 + 2 * (size_t)kSubtreeSmemCells * sizeof(LCell);
 
-// Largest cell (points) the subtree kernel holds for d coordinates: keys
-// (4d bytes), permutation (4), subset id (2), two orders, cell ids and the
-// scan (2 each, +2 once).
+// Column stride (elements) of a cell of N points in shared memory: room for
+// the 16-byte alignment phase of the bulk copies.
+__host__ __device__ inline uint32_t subtree_stride(uint32_t N) { return (N + 8 + 3) & ~3u; }
+
+// Bytes of shared memory a cell of N points with d coordinates needs beyond
+// the fixed part: d key columns and the permutation at the padded stride, the
+// gathered keys (4 bytes), the subset ids, two orders, cell ids, the scan and
+// the bin / flag array (2 bytes each).
+__host__ __device__ inline size_t subtree_point_bytes(uint32_t N, int d) {
+  const size_t stride = subtree_stride(N);
+  return (size_t)(d + 1) * stride * 4 + (((size_t)N * 4 + 15) & ~(size_t)15) +
+         6 * ((((size_t)N + 1) * 2 + 15) & ~(size_t)15);
+}
+
+// Largest cell (points) the subtree kernel holds for d coordinates.
 inline int subtree_capacity(int d) {
-  const size_t per_point = 4 * (size_t)d + 14;
-  size_t cap = (kSubtreeSmemBytes - kSubtreeFixedBytes - 2) / per_point;
-  if (cap > 8192) cap = 8192;
-  cap &= ~(size_t)31;
-  return (int)cap;
+  int lo = 32, hi = 8192;
+  if (kSubtreeFixedBytes + subtree_point_bytes(lo, d) > kSubtreeSmemBytes) return 0;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (kSubtreeFixedBytes + subtree_point_bytes(mid, d) <= kSubtreeSmemBytes) lo = mid; else hi = mid - 1;
+  }
+  return lo & ~31;
 }
 
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
-                     uint32_t max_bigseg, bool any_widest, cudaStream_t st);
+                     uint32_t max_bigseg, bool need_root_dims, bool any_widest, int max_d, uint64_t points,
+                     cudaStream_t st);
 
 cudaError_t prepare_subtree_kernel();
 void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head, LCell* slices,
-                    uint32_t slice_cells, uint32_t grid, cudaStream_t st);
+                    uint32_t slice_cells, uint32_t grid, uint64_t points, cudaStream_t st);
 
 void launch_iota(uint32_t* out, uint32_t n, cudaStream_t st);
 

@@ -3,22 +3,31 @@
 //
 // For every big cell c of the step (paper, Sec. 2: a level splits each of its
 // cells along the key coordinate t at a median):
-//   1. key coordinate: cyclic (Sec. 1) or widest range (Sec. 1, Friedman rule)
+//   1. key coordinate: cyclic (Sec. 1) or widest range (Sec. 1, Friedman
+//      rule; computed for the root here, for every other cell by the parent's
+//      scatter, which reduces each child's per-coordinate min and max while it
+//      moves the columns);
 //   2. per (cell, subset) segment: count, then the keys grouped by segment
-//      into a scratch array (the subsets of Sec. 3.2 / App. C.2)
-//   3. per segment: the exact lower median (8-bit MSD radix select)
-//   4. per cell: the count-weighted lower median of the segment medians
+//      into a scratch array (the subsets of Sec. 3.2 / App. C.2);
+//   3. per segment: the exact lower median (8-bit MSD radix select);
+//   4. per cell: the count-weighted lower median of the segment medians;
 //   5. stable partition of all d columns, the permutation and the subset ids
-//      around the split (key <= split to the left), via per-tile counts and a
-//      per-cell scan of them
-//   6. children: terminal / small (subtree kernel) / big (next step)
-// Work is split into tiles of kTile points of one cell.
+//      around the split (key <= split to the left) from per-tile counts and a
+//      per-cell scan of them;
+//   6. children: terminal / small (subtree kernel) / big (next step).
+// Work is split into tiles of kTile points of one cell; a thread owns kItems
+// points of a tile (strided by the block size, so every load is coalesced)
+// and issues all of its loads before it uses any of them.
 #include "kdt_internal.cuh"
 #include "kdt_launch.h"
+#include "kdt_trace.h"
 
 namespace kdt {
 
 namespace {
+
+constexpr int kItems = kTile / kTileThreads;
+constexpr int kWarps = kTileThreads / 32;
 
 __device__ __forceinline__ bool tile_of(const StepDev& s, uint32_t tile, uint2* out) {
   if (tile >= *s.ntiles_total) return false;
@@ -26,10 +35,46 @@ __device__ __forceinline__ bool tile_of(const StepDev& s, uint32_t tile, uint2* 
   return true;
 }
 
+// Subset ids of a thread's points: raw loads first, then the mapping.
+__device__ __forceinline__ void load_subsets(const TreeDev& t, const void* S, const uint32_t* P,
+                                             uint32_t begin, uint32_t i0, uint32_t end,
+                                             uint32_t (&sub)[kItems]) {
+  uint32_t raw[kItems];
+#pragma unroll
+  for (int q = 0; q < kItems; ++q) {
+    const uint32_t i = i0 + threadIdx.x + q * kTileThreads;
+    const int64_t p = (int64_t)begin + i;
+    raw[q] = 0;
+    if (i < end) {
+      if (t.subset_mode == SUB_EXPLICIT)
+        raw[q] = t.sid_bytes == 1 ? (uint32_t)((const uint8_t*)S)[p] : (uint32_t)((const uint16_t*)S)[p];
+      else
+        raw[q] = P ? P[p] : (uint32_t)p;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kItems; ++q) {
+    const uint32_t i = i0 + threadIdx.x + q * kTileThreads;
+    sub[q] = 0xffffffffu;
+    if (i < end) {
+      if (t.subset_mode == SUB_MOD) {
+        sub[q] = raw[q] % (uint32_t)t.r;
+      } else if (t.subset_mode == SUB_CONTIG) {
+        sub[q] = (uint32_t)(((uint64_t)raw[q] * (uint64_t)t.r) / (uint64_t)t.n);
+      } else if (raw[q] < (uint32_t)t.r) {
+        sub[q] = raw[q];
+      } else {
+        set_status(t, ST_INVALID_ARG);
+        sub[q] = 0;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- prep
 
-// Single CTA: per-cell tile and segment counts, exclusive scans, key dim for
-// cyclic keys.
+// Single CTA: per-cell tile and segment counts, exclusive scans, key dims
+// that are already known.
 __global__ void k_prep(const TreeDev* trees, StepDev s) {
   __shared__ uint32_t tmp[33];
   uint32_t tile_run = 0, seg_run = 0;
@@ -41,7 +86,10 @@ __global__ void k_prep(const TreeDev* trees, StepDev s) {
       const TreeDev& t = trees[cell.tree];
       nt = (cell.count + kTile - 1) / kTile;
       ns = (uint32_t)t.r;
-      if (t.key_rule == KEY_CYCLIC) s.kdim[c] = (uint32_t)(cell.level % t.d);
+      if (t.key_rule == KEY_CYCLIC)
+        s.kdim[c] = (uint32_t)(cell.level % t.d);
+      else if (cell.dim >= 0)
+        s.kdim[c] = (uint32_t)cell.dim;
     }
     uint32_t tot_t, tot_s;
     const uint32_t et = block_excl_scan(nt, tmp, &tot_t);
@@ -62,75 +110,90 @@ __global__ void k_prep(const TreeDev* trees, StepDev s) {
 }
 
 // One CTA per cell: tile list entries and zeroed segment counts.
-__global__ void k_tiles(const TreeDev* trees, StepDev s) {
+__global__ void k_tiles(StepDev s) {
   const uint32_t c = blockIdx.x;
-  const Cell cell = s.cells[c];
   const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
   for (uint32_t j = tb + threadIdx.x; j < te; j += blockDim.x)
     s.tiles[j] = make_uint2(c, (j - tb) * (uint32_t)kTile);
   const uint32_t sb = s.seg_base[c], se = s.seg_base[c + 1];
   for (uint32_t g = sb + threadIdx.x; g < se; g += blockDim.x) s.seg_w[g] = 0;
-  (void)trees;
-  (void)cell;
 }
 
 // ------------------------------------------------------- widest spread
 
-// Per tile and coordinate: min and max key (partials; reduced per cell below).
+// Per tile and coordinate of a cell whose key coordinate is not known yet
+// (the root): min and max key, reduced per cell by k_pick_dim.
 __global__ void __launch_bounds__(kTileThreads) k_minmax(const TreeDev* trees, StepDev s) {
   uint2 tl;
   if (!tile_of(s, blockIdx.x, &tl)) return;
-  __shared__ uint32_t red[2][kTileThreads / 32];
   const Cell cell = s.cells[tl.x];
   const TreeDev& t = trees[cell.tree];
-  const float* X = src_cols(t, cell.level);
+  if (t.key_rule != KEY_WIDEST || cell.dim >= 0) return;
+  __shared__ uint32_t red[2][kWarps];
+  const float* X = src_cols(t, cell.level) + cell.begin;
   const int64_t n = t.n;
   const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool nan = false;
   for (int l = 0; l < t.d; ++l) {
-    uint32_t lo = 0xffffffffu, hi = 0u;
-    for (uint32_t i = tl.y + threadIdx.x; i < end; i += blockDim.x) {
-      const float x = X[(int64_t)l * n + cell.begin + i];
-      if (is_nan_bits(x)) set_status(t, ST_NAN_INPUT);
-      const uint32_t k = ord_key(x);
-      lo = min(lo, k);
-      hi = max(hi, k);
+    float x[kItems];
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+      x[q] = i < end ? X[(int64_t)l * n + i] : 0.0f;
     }
-    lo = warp_min(lo);
-    hi = warp_max(hi);
+    uint32_t lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+      if (i < end) {
+        nan |= is_nan_bits(x[q]);
+        const uint32_t k = ord_key(x[q]);
+        lo = min(lo, k);
+        hi = max(hi, k);
+      }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
     if (lane == 0) {
       red[0][warp] = lo;
       red[1][warp] = hi;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      for (int w = 1; w < kWarps; ++w) {
         lo = min(lo, red[0][w]);
         hi = max(hi, red[1][w]);
       }
-      s.tile_mm[((size_t)blockIdx.x * kMaxDims + l) * 2 + 0] = lo;
-      s.tile_mm[((size_t)blockIdx.x * kMaxDims + l) * 2 + 1] = hi;
+      s.tile_mm[((size_t)blockIdx.x * 2 * kMaxDims + l) * 2 + 0] = lo;
+      s.tile_mm[((size_t)blockIdx.x * 2 * kMaxDims + l) * 2 + 1] = hi;
     }
     __syncthreads();
   }
+  if (nan) set_status(t, ST_NAN_INPUT);
 }
 
-// One CTA per cell: reduce the tile partials and pick the widest coordinate
-// (range (double)max - (double)min; 0 when max and min are the same key;
-// lowest coordinate on ties).
+// Range of a coordinate from its min and max keys: (double)max - (double)min,
+// 0 when both are the same key.
+__device__ __forceinline__ double key_range(uint32_t lo, uint32_t hi) {
+  return (lo == hi) ? 0.0 : (double)key_float(hi) - (double)key_float(lo);
+}
+
+// One CTA per cell with an unknown widest coordinate: reduce the tile
+// partials and pick the coordinate of largest range (lowest on ties).
 __global__ void k_pick_dim(const TreeDev* trees, StepDev s) {
   const uint32_t c = blockIdx.x;
   const Cell cell = s.cells[c];
   const TreeDev& t = trees[cell.tree];
-  if (t.key_rule != KEY_WIDEST) return;
+  if (t.key_rule != KEY_WIDEST || cell.dim >= 0) return;
   __shared__ uint32_t slo[kMaxDims], shi[kMaxDims];
   const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int l = warp; l < t.d; l += nw) {
     uint32_t lo = 0xffffffffu, hi = 0u;
     for (uint32_t j = tb + lane; j < te; j += 32) {
-      lo = min(lo, s.tile_mm[((size_t)j * kMaxDims + l) * 2 + 0]);
-      hi = max(hi, s.tile_mm[((size_t)j * kMaxDims + l) * 2 + 1]);
+      lo = min(lo, s.tile_mm[((size_t)j * 2 * kMaxDims + l) * 2 + 0]);
+      hi = max(hi, s.tile_mm[((size_t)j * 2 * kMaxDims + l) * 2 + 1]);
     }
     lo = warp_min(lo);
     hi = warp_max(hi);
@@ -144,8 +207,7 @@ __global__ void k_pick_dim(const TreeDev* trees, StepDev s) {
     int best = 0;
     double best_range = -1.0;
     for (int l = 0; l < t.d; ++l) {
-      const double range =
-          (slo[l] == shi[l]) ? 0.0 : (double)key_float(shi[l]) - (double)key_float(slo[l]);
+      const double range = key_range(slo[l], shi[l]);
       if (range > best_range) {
         best_range = range;
         best = l;
@@ -166,16 +228,14 @@ __global__ void __launch_bounds__(kTileThreads) k_seg_count(const TreeDev* trees
   const Cell cell = s.cells[tl.x];
   const TreeDev& t = trees[cell.tree];
   const int r = t.r;
-  const uint32_t* P = src_perm(t, cell.level);
-  const void* S = src_sid(t, cell.level);
+  const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
+  uint32_t sub[kItems];
+  load_subsets(t, src_sid(t, cell.level), src_perm(t, cell.level), cell.begin, tl.y, end, sub);
   for (int j = threadIdx.x; j < r; j += blockDim.x) hist[j] = 0;
   __syncthreads();
-  const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
-  for (uint32_t i = tl.y + threadIdx.x; i < end; i += blockDim.x) {
-    const int64_t p = (int64_t)cell.begin + i;
-    const uint32_t orig = P ? P[p] : (uint32_t)p;
-    atomicAdd(&hist[subset_of(t, S, orig, p)], 1u);
-  }
+#pragma unroll
+  for (int q = 0; q < kItems; ++q)
+    if (sub[q] != 0xffffffffu) atomicAdd(&hist[sub[q]], 1u);
   __syncthreads();
   uint32_t* w = s.seg_w + s.seg_base[tl.x];
   for (int j = threadIdx.x; j < r; j += blockDim.x)
@@ -209,7 +269,6 @@ __global__ void k_seg_scan(const TreeDev* trees, StepDev s) {
 
 // Per tile: copy the keys of the tile's points into the scratch array grouped
 // by subset (order inside a segment is irrelevant to its median).
-constexpr int kPerThread = kTile / kTileThreads;
 __global__ void __launch_bounds__(kTileThreads) k_group(const TreeDev* trees, StepDev s) {
   uint2 tl;
   if (!tile_of(s, blockIdx.x, &tl)) return;
@@ -217,34 +276,30 @@ __global__ void __launch_bounds__(kTileThreads) k_group(const TreeDev* trees, St
   const Cell cell = s.cells[tl.x];
   const TreeDev& t = trees[cell.tree];
   const int r = t.r;
-  const uint32_t dim = s.kdim[tl.x];
-  const float* X = src_cols(t, cell.level) + (int64_t)dim * t.n;
-  const uint32_t* P = src_perm(t, cell.level);
-  const void* S = src_sid(t, cell.level);
+  const float* X = src_cols(t, cell.level) + (int64_t)s.kdim[tl.x] * t.n + cell.begin;
+  const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
+  float x[kItems];
+#pragma unroll
+  for (int q = 0; q < kItems; ++q) {
+    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+    x[q] = i < end ? X[i] : 0.0f;
+  }
+  uint32_t sub[kItems];
+  load_subsets(t, src_sid(t, cell.level), src_perm(t, cell.level), cell.begin, tl.y, end, sub);
   for (int j = threadIdx.x; j < r; j += blockDim.x) cnt[j] = 0;
   __syncthreads();
-  const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
-  uint32_t key[kPerThread], sub[kPerThread], lr[kPerThread];
+  uint32_t lr[kItems];
 #pragma unroll
-  for (int q = 0; q < kPerThread; ++q) {
-    const uint32_t i = tl.y + threadIdx.x + q * blockDim.x;
-    sub[q] = 0xffffffffu;
-    if (i < end) {
-      const int64_t p = (int64_t)cell.begin + i;
-      const uint32_t orig = P ? P[p] : (uint32_t)p;
-      sub[q] = subset_of(t, S, orig, p);
-      key[q] = ord_key(X[p]);
-      lr[q] = atomicAdd(&cnt[sub[q]], 1u);
-    }
-  }
+  for (int q = 0; q < kItems; ++q)
+    lr[q] = sub[q] != 0xffffffffu ? atomicAdd(&cnt[sub[q]], 1u) : 0u;
   __syncthreads();
   uint32_t* cur = s.seg_cur + s.seg_base[tl.x];
   for (int j = threadIdx.x; j < r; j += blockDim.x)
     if (cnt[j]) cnt[j] = atomicAdd(&cur[j], cnt[j]);  // now: base position of this tile's run
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < kPerThread; ++q)
-    if (sub[q] != 0xffffffffu) t.keys[cnt[sub[q]] + lr[q]] = key[q];
+  for (int q = 0; q < kItems; ++q)
+    if (sub[q] != 0xffffffffu) t.keys[cnt[sub[q]] + lr[q]] = ord_key(x[q]);
 }
 
 // ------------------------------------------------------------ selection
@@ -257,7 +312,15 @@ __device__ uint32_t warp_radix_select(const uint32_t* keys, uint32_t w, uint32_t
   for (int shift = 24; shift >= 0; shift -= 8) {
     for (int i = lane; i < 256; i += 32) hist[i] = 0;
     __syncwarp();
-    for (uint32_t i = lane; i < w; i += 32) {
+    uint32_t i = lane;
+    for (; i + 96 < w; i += 128) {
+      const uint32_t k0 = keys[i], k1 = keys[i + 32], k2 = keys[i + 64], k3 = keys[i + 96];
+      if ((k0 & mask) == prefix) atomicAdd(&hist[(k0 >> shift) & 255u], 1u);
+      if ((k1 & mask) == prefix) atomicAdd(&hist[(k1 >> shift) & 255u], 1u);
+      if ((k2 & mask) == prefix) atomicAdd(&hist[(k2 >> shift) & 255u], 1u);
+      if ((k3 & mask) == prefix) atomicAdd(&hist[(k3 >> shift) & 255u], 1u);
+    }
+    for (; i < w; i += 32) {
       const uint32_t k = keys[i];
       if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
     }
@@ -318,7 +381,16 @@ __global__ void __launch_bounds__(256) k_select_big(const TreeDev* trees, StepDe
   for (int shift = 24; shift >= 0; shift -= 8) {
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < w; i += blockDim.x) {
+    uint32_t i = threadIdx.x;
+    for (; i + 7 * 256 < w; i += 8 * 256) {
+      uint32_t k[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) k[q] = keys[i + q * 256];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if ((k[q] & mask) == prefix) atomicAdd(&hist[(k[q] >> shift) & 255u], 1u);
+    }
+    for (; i < w; i += 256) {
       const uint32_t k = keys[i];
       if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
     }
@@ -389,18 +461,32 @@ __global__ void __launch_bounds__(256) k_combine(const TreeDev* trees, StepDev s
 __global__ void __launch_bounds__(kTileThreads) k_part_count(const TreeDev* trees, StepDev s) {
   uint2 tl;
   if (!tile_of(s, blockIdx.x, &tl)) return;
+  __shared__ uint32_t red[kWarps];
   const Cell cell = s.cells[tl.x];
   const TreeDev& t = trees[cell.tree];
   const float* X = src_cols(t, cell.level) + (int64_t)s.kdim[tl.x] * t.n + cell.begin;
   const uint32_t m = s.mkey[tl.x];
   const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
-  uint32_t cnt = 0;
-  for (uint32_t i0 = tl.y; i0 < end; i0 += blockDim.x) {
-    const uint32_t i = i0 + threadIdx.x;
-    const bool left = i < end && ord_key(X[i]) <= m;
-    cnt += __syncthreads_count(left);
+  float x[kItems];
+#pragma unroll
+  for (int q = 0; q < kItems; ++q) {
+    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+    x[q] = i < end ? X[i] : 0.0f;
   }
-  if (threadIdx.x == 0) s.tile_left[blockIdx.x] = cnt;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int q = 0; q < kItems; ++q) {
+    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+    cnt += (i < end) && ord_key(x[q]) <= m;
+  }
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < kWarps; ++w) tot += red[w];
+    s.tile_left[blockIdx.x] = tot;
+  }
 }
 
 // One CTA per cell: exclusive scan of its tiles' left counts.
@@ -421,18 +507,23 @@ __global__ void k_part_scan(StepDev s) {
 }
 
 // Per tile: stable scatter of all columns, the permutation and the subset ids.
-// Left points of the tile go to begin + (left points before the tile) + rank,
-// right points to begin + L + (right points before the tile) + rank.
+// Point j of the tile (in position order) goes left to
+//   begin + (left points before the tile) + (left points before j in the tile)
+// or right to
+//   begin + L + (right points before the tile) + (right points before j).
+// A child that is terminal only receives the permutation, in out_perm. For
+// widest spread the tile also reduces each child's min and max per coordinate.
 __global__ void __launch_bounds__(kTileThreads) k_part_scatter(const TreeDev* trees, StepDev s) {
   uint2 tl;
   if (!tile_of(s, blockIdx.x, &tl)) return;
-  __shared__ uint32_t wsum[kTileThreads / 32];
+  __shared__ uint32_t wcnt[kItems][kWarps];
+  __shared__ uint32_t wmm[kWarps][2][kMaxDims][2];
   const Cell cell = s.cells[tl.x];
   const TreeDev& t = trees[cell.tree];
   const int level = cell.level;
   const int64_t n = t.n;
   const int d = t.d;
-  const float* X = src_cols(t, level);
+  const float* X = src_cols(t, level) + cell.begin;
   const uint32_t* P = src_perm(t, level);
   const void* S = src_sid(t, level);
   float* Xo = t.xbuf[level & 1];
@@ -443,59 +534,174 @@ __global__ void __launch_bounds__(kTileThreads) k_part_scatter(const TreeDev* tr
   const uint32_t m = s.mkey[tl.x];
   const uint32_t loff = s.tile_loff[blockIdx.x];
   const uint32_t L = s.lcount[tl.x];
-  uint32_t lnext = cell.begin + loff;
-  uint32_t rnext = cell.begin + L + (tl.y - loff);
-  // A child that is terminal is never read again: its points only need their
-  // original index in the final order.
-  const int child_stall = (cell.count == L) ? cell.stall + 1 : 0;
-  const bool term_left = is_terminal(t, L, level + 1, child_stall);
-  const bool term_right = is_terminal(t, cell.count - L, level + 1, child_stall);
   const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
+  // children that are terminal are never read again
+  const int child_stall = (cell.count == L) ? cell.stall + 1 : 0;
+  const bool term_left = is_terminal(t, L, level + 1, child_stall);
+  const bool term_right = is_terminal(t, cell.count - L, level + 1, child_stall);
+  const bool want_mm = t.key_rule == KEY_WIDEST && !(term_left && term_right);
+
+  // flags of the thread's points
+  float xk[kItems];
+#pragma unroll
+  for (int q = 0; q < kItems; ++q) {
+    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+    xk[q] = i < end ? X[(int64_t)dim * n + i] : 0.0f;
+  }
+  bool left[kItems];
+  unsigned bal[kItems];
+#pragma unroll
+  for (int q = 0; q < kItems; ++q) {
+    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+    left[q] = i < end && ord_key(xk[q]) <= m;
+    bal[q] = __ballot_sync(0xffffffffu, left[q]);
+    if (lane == 0) wcnt[q][warp] = __popc(bal[q]);
+  }
+  if (want_mm) {
+    for (int j = lane; j < 2 * d * 2; j += 32) {
+      const int side = j / (2 * d), l = (j / 2) % d, which = j & 1;
+      wmm[warp][side][l][which] = which ? 0u : 0xffffffffu;
+    }
+  }
+  __syncthreads();
+  // destinations, in position order: rounds q, then warps, then lanes
+  uint32_t dst[kItems];
+  {
+    uint32_t before = 0;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      uint32_t in_round = 0, below_warp = 0;
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t v = wcnt[q][w];
+        below_warp += (w < warp) ? v : 0u;
+        in_round += v;
+      }
+      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+      const uint32_t lrank = before + below_warp + __popc(bal[q] & lt_mask);
+      const uint32_t rrank = (i - tl.y) - lrank;  // right points of the tile before this one
+      dst[q] = left[q] ? cell.begin + loff + lrank : cell.begin + L + (tl.y - loff) + rrank;
+      before += in_round;
+    }
+  }
   bool saw_nan = false;
-  for (uint32_t i0 = tl.y; i0 < end; i0 += blockDim.x) {
-    const uint32_t i = i0 + threadIdx.x;
-    const bool valid = i < end;
-    const int64_t p = (int64_t)cell.begin + i;
-    bool left = false;
-    if (valid) left = ord_key(X[(int64_t)dim * n + p]) <= m;
-    const unsigned bal = __ballot_sync(0xffffffffu, left);
-    if (lane == 0) wsum[warp] = __popc(bal);
-    __syncthreads();
-    uint32_t before = 0, total = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      const uint32_t v = wsum[w];
-      before += (w < warp) ? v : 0u;
-      total += v;
+  // permutation
+  {
+    uint32_t pv[kItems];
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+      const int64_t p = (int64_t)cell.begin + i;
+      pv[q] = (i < end) ? (P ? P[p] : (uint32_t)p) : 0u;
     }
-    const uint32_t lrank = before + __popc(bal & lt_mask);
-    const uint32_t nvalid = min((uint32_t)blockDim.x, end - i0);
-    if (valid && (left ? term_left : term_right)) {
-      const uint32_t dst = left ? lnext + lrank : rnext + (threadIdx.x - lrank);
-      t.out_perm[dst] = P ? P[p] : (uint32_t)p;
-      if (level == 0)
-        for (int l = 0; l < d; ++l) saw_nan |= is_nan_bits(X[(int64_t)l * n + p]);
-    } else if (valid) {
-      const uint32_t dst = left ? lnext + lrank : rnext + (threadIdx.x - lrank);
-      for (int l = 0; l < d; ++l) {
-        const float x = X[(int64_t)l * n + p];
-        saw_nan |= is_nan_bits(x);
-        Xo[(int64_t)l * n + dst] = x;
-      }
-      Po[dst] = P ? P[p] : (uint32_t)p;
-      if (explicit_sid) {
-        if (t.sid_bytes == 1)
-          ((uint8_t*)So)[dst] = ((const uint8_t*)S)[p];
-        else
-          ((uint16_t*)So)[dst] = ((const uint16_t*)S)[p];
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+      if (i >= end) continue;
+      if (left[q] ? term_left : term_right)
+        t.out_perm[dst[q]] = pv[q];
+      else
+        Po[dst[q]] = pv[q];
+    }
+  }
+  // coordinates
+  for (int l = 0; l < d; ++l) {
+    float x[kItems];
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+      x[q] = (i < end) ? (l == (int)dim ? xk[q] : X[(int64_t)l * n + i]) : 0.0f;
+    }
+    uint32_t lmin = 0xffffffffu, lmax = 0u, rmin = 0xffffffffu, rmax = 0u;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+      if (i >= end) continue;
+      if (level == 0) saw_nan |= is_nan_bits(x[q]);
+      if (left[q] ? term_left : term_right) continue;
+      Xo[(int64_t)l * n + dst[q]] = x[q];
+      if (want_mm) {
+        const uint32_t k = ord_key(x[q]);
+        if (left[q]) {
+          lmin = min(lmin, k);
+          lmax = max(lmax, k);
+        } else {
+          rmin = min(rmin, k);
+          rmax = max(rmax, k);
+        }
       }
     }
-    lnext += total;
-    rnext += nvalid - total;
-    __syncthreads();
+    if (want_mm) {
+      lmin = __reduce_min_sync(0xffffffffu, lmin);
+      lmax = __reduce_max_sync(0xffffffffu, lmax);
+      rmin = __reduce_min_sync(0xffffffffu, rmin);
+      rmax = __reduce_max_sync(0xffffffffu, rmax);
+      if (lane == 0) {
+        wmm[warp][0][l][0] = lmin;
+        wmm[warp][0][l][1] = lmax;
+        wmm[warp][1][l][0] = rmin;
+        wmm[warp][1][l][1] = rmax;
+      }
+    }
+  }
+  // subset ids
+  if (explicit_sid) {
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+      if (i >= end || (left[q] ? term_left : term_right)) continue;
+      const int64_t p = (int64_t)cell.begin + i;
+      if (t.sid_bytes == 1)
+        ((uint8_t*)So)[dst[q]] = ((const uint8_t*)S)[p];
+      else
+        ((uint16_t*)So)[dst[q]] = ((const uint16_t*)S)[p];
+    }
   }
   if (saw_nan) set_status(t, ST_NAN_INPUT);
+  if (want_mm) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < 2 * d * 2; j += blockDim.x) {
+      const int side = j / (2 * d), l = (j / 2) % d, which = j & 1;
+      uint32_t v = wmm[0][side][l][which];
+      for (int w = 1; w < kWarps; ++w) {
+        const uint32_t u = wmm[w][side][l][which];
+        v = which ? max(v, u) : min(v, u);
+      }
+      s.tile_mm[(((size_t)blockIdx.x * 2 + side) * kMaxDims + l) * 2 + which] = v;
+    }
+  }
+}
+
+// Grid (cell, side, coordinate): reduce the scatter's tile partials to each
+// child's min and max key per coordinate (widest spread only).
+__global__ void k_child_mm(const TreeDev* trees, StepDev s) {
+  const uint32_t c = blockIdx.x, side = blockIdx.y, l = blockIdx.z;
+  const Cell cell = s.cells[c];
+  const TreeDev& t = trees[cell.tree];
+  if (t.key_rule != KEY_WIDEST || (int)l >= t.d) return;
+  __shared__ uint32_t red[2][8];
+  const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  for (uint32_t j = tb + threadIdx.x; j < te; j += blockDim.x) {
+    lo = min(lo, s.tile_mm[(((size_t)j * 2 + side) * kMaxDims + l) * 2 + 0]);
+    hi = max(hi, s.tile_mm[(((size_t)j * 2 + side) * kMaxDims + l) * 2 + 1]);
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = lo;
+    red[1][threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      lo = min(lo, red[0][w]);
+      hi = max(hi, red[1][w]);
+    }
+    s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 0] = lo;
+    s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 1] = hi;
+  }
 }
 
 // ------------------------------------------------------------- children
@@ -521,13 +727,29 @@ __global__ void k_next(const TreeDev* trees, StepDev s) {
       set_status(t, ST_LEVEL_CAP);
       continue;
     }
-    const Cell child{cb[side], cc[side], heap, cell.tree, (int16_t)level, (int16_t)stall};
+    int16_t dim = -1;
+    if (t.key_rule == KEY_WIDEST) {
+      int best = 0;
+      double best_range = -1.0;
+      for (int l = 0; l < t.d; ++l) {
+        const double range = key_range(s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 0],
+                                       s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 1]);
+        if (range > best_range) {
+          best_range = range;
+          best = l;
+        }
+      }
+      dim = (int16_t)best;
+    }
+    const Cell child{cb[side], cc[side], heap, cell.tree, (int8_t)level, (int8_t)stall, dim};
     if (cc[side] <= (uint32_t)t.small_max) {
       const uint32_t slot = atomicAdd(s.small_count, 1u);
       if (slot < s.small_cap) s.small[slot] = child; else set_status(t, ST_CAPACITY);
+      atomicAdd(s.small_points, cc[side]);
     } else {
       const uint32_t slot = atomicAdd(s.next_big_count, 1u);
       if (slot < s.next_big_cap) s.next_big[slot] = child; else set_status(t, ST_CAPACITY);
+      atomicAdd(s.next_big_points, cc[side]);
     }
   }
 }
@@ -537,25 +759,36 @@ __global__ void k_next(const TreeDev* trees, StepDev s) {
 // ------------------------------------------------------------ launcher
 
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
-                     uint32_t max_bigseg, bool any_widest, cudaStream_t st) {
+                     uint32_t max_bigseg, bool need_root_dims, bool any_widest, int max_d, uint64_t points,
+                     cudaStream_t st) {
   const uint32_t nc = s.ncells;
   if (nc == 0) return;
-  k_prep<<<1, 1024, 0, st>>>(trees, s);
-  k_tiles<<<nc, 256, 0, st>>>(trees, s);
-  if (any_widest) {
-    k_minmax<<<max_tiles, kTileThreads, 0, st>>>(trees, s);
-    k_pick_dim<<<nc, 256, 0, st>>>(trees, s);
+  { TraceScope ts(K_PREP, st); k_prep<<<1, 1024, 0, st>>>(trees, s); }
+  { TraceScope ts(K_TILES, st); k_tiles<<<nc, 256, 0, st>>>(s); }
+  if (need_root_dims) {
+    { TraceScope ts(K_MINMAX, st, points); k_minmax<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
+    { TraceScope ts(K_PICK_DIM, st); k_pick_dim<<<nc, 256, 0, st>>>(trees, s); }
   }
-  k_seg_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s);
-  k_seg_scan<<<nc, 256, 0, st>>>(trees, s);
-  k_group<<<max_tiles, kTileThreads, 0, st>>>(trees, s);
-  k_select_small<<<(nseg + 7) / 8, 256, 0, st>>>(trees, s, nseg);
-  if (max_bigseg) k_select_big<<<max_bigseg, 256, 0, st>>>(trees, s);
-  k_combine<<<nc, 256, 0, st>>>(trees, s);
-  k_part_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s);
-  k_part_scan<<<nc, 1024, 0, st>>>(s);
-  k_part_scatter<<<max_tiles, kTileThreads, 0, st>>>(trees, s);
-  k_next<<<(nc + 255) / 256, 256, 0, st>>>(trees, s);
+  { TraceScope ts(K_SEG_COUNT, st, points); k_seg_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
+  { TraceScope ts(K_SEG_SCAN, st); k_seg_scan<<<nc, 256, 0, st>>>(trees, s); }
+  { TraceScope ts(K_GROUP, st, points); k_group<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
+  {
+    TraceScope ts(K_SELECT_SMALL, st, points);
+    k_select_small<<<(nseg + 7) / 8, 256, 0, st>>>(trees, s, nseg);
+  }
+  if (max_bigseg) { TraceScope ts(K_SELECT_BIG, st); k_select_big<<<max_bigseg, 256, 0, st>>>(trees, s); }
+  { TraceScope ts(K_COMBINE, st); k_combine<<<nc, 256, 0, st>>>(trees, s); }
+  { TraceScope ts(K_PART_COUNT, st, points); k_part_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
+  { TraceScope ts(K_PART_SCAN, st); k_part_scan<<<nc, 1024, 0, st>>>(s); }
+  {
+    TraceScope ts(K_PART_SCATTER, st, points);
+    k_part_scatter<<<max_tiles, kTileThreads, 0, st>>>(trees, s);
+  }
+  if (any_widest) {
+    TraceScope ts(K_CHILD_MM, st);
+    k_child_mm<<<dim3(nc, 2, max_d), 256, 0, st>>>(trees, s);
+  }
+  { TraceScope ts(K_NEXT, st); k_next<<<(nc + 255) / 256, 256, 0, st>>>(trees, s); }
 }
 
 }  // namespace kdt

@@ -1,0 +1,34 @@
+// kdt_trace.h -- launch counting and optional per-kernel CUDA-event timing.
+//
+// Every kernel launch of the library goes through a TraceScope. Launches are
+// always counted; when tracing is enabled (kdt_trace_enable), the scope also
+// records a CUDA event before and after the launch on the launching stream,
+// and kdt_trace_read turns the pairs into per-kernel totals.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kdt {
+
+enum KernelId {
+  K_PREP, K_TILES, K_MINMAX, K_PICK_DIM, K_SEG_COUNT, K_SEG_SCAN, K_GROUP, K_SELECT_SMALL,
+  K_SELECT_BIG, K_COMBINE, K_PART_COUNT, K_PART_SCAN, K_PART_SCATTER, K_CHILD_MM, K_NEXT,
+  K_SUBTREE, K_FINALIZE, K_IOTA, K_BATCH_SEED, K_NUM
+};
+
+class TraceScope {
+ public:
+  // units: work items the launch processes (points), for bandwidth figures
+  TraceScope(KernelId id, cudaStream_t st, uint64_t units = 0);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+
+ private:
+  KernelId id_;
+  cudaStream_t st_;
+  uint64_t units_;
+  cudaEvent_t start_ = nullptr;
+};
+
+}  // namespace kdt

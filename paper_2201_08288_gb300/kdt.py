@@ -31,13 +31,19 @@ STATUS_NAMES = {0: "KDT_OK", 1: "KDT_ERR_INVALID_ARG", 2: "KDT_ERR_NAN_INPUT", 3
 
 # Every symbol include/kdt.h declares (checked by the CPU test suite).
 EXPORTED = ["kdt_workspace_size", "kdt_build", "kdt_workspace_size_host", "kdt_build_host",
-            "kdt_subtree_capacity", "kdt_status_str"]
+            "kdt_subtree_capacity", "kdt_status_str", "kdt_trace_enable", "kdt_launch_count",
+            "kdt_trace_read"]
 
 
 class KdtError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}")
         self.status = status
+
+
+class kdt_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("units", ctypes.c_uint64)]
 
 
 class kdt_params(ctypes.Structure):
@@ -81,6 +87,12 @@ def load_library(path: str = LIB_PATH):
     lib.kdt_subtree_capacity.restype = ctypes.c_int32
     lib.kdt_status_str.argtypes = [ctypes.c_int]
     lib.kdt_status_str.restype = ctypes.c_char_p
+    lib.kdt_trace_enable.argtypes = [ctypes.c_int32]
+    lib.kdt_trace_enable.restype = None
+    lib.kdt_launch_count.argtypes = []
+    lib.kdt_launch_count.restype = ctypes.c_uint64
+    lib.kdt_trace_read.argtypes = [ctypes.POINTER(kdt_kernel_stat), ctypes.c_int32, ctypes.c_int32]
+    lib.kdt_trace_read.restype = ctypes.c_int32
     _lib = lib
     return lib
 
@@ -118,6 +130,23 @@ def kdt_subtree_capacity(d: int) -> int:
 
 def kdt_status_str(st: int) -> str:
     return load_library().kdt_status_str(st).decode()
+
+
+def kdt_trace_enable(on: bool) -> None:
+    load_library().kdt_trace_enable(1 if on else 0)
+
+
+def kdt_launch_count() -> int:
+    return int(load_library().kdt_launch_count())
+
+
+def kdt_trace_read(reset: bool = True) -> dict:
+    """Per-kernel {name: (launches, total_ms, points)} of the traced launches."""
+    lib = load_library()
+    buf = (kdt_kernel_stat * 64)()
+    k = lib.kdt_trace_read(buf, 64, 1 if reset else 0)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), int(buf[i].units))
+            for i in range(min(k, 64))}
 
 
 @dataclass
