@@ -158,6 +158,28 @@ uint64_t kdt_launch_count(void);
  * with data. Synchronises on the recorded events. reset != 0 clears totals. */
 int32_t kdt_trace_read(kdt_kernel_stat *out, int32_t max, int32_t reset);
 
+/*
+ * kdt_build without any memory allocation, for callers that cannot call
+ * cudaMalloc (for example a host application that runs this library under a
+ * fixed device-memory budget owned by its own allocator, or a latency-critical
+ * path that cannot afford cudaMalloc's cost and implicit synchronisation). The
+ * paper has no counterpart: this is a property of the library, not of the
+ * method.
+ *   The workspace is a 64 MiB array in device memory that the library defines
+ *   statically; every GPU that loads the library keeps it until the process
+ *   exits. Problems whose kdt_workspace_size exceeds 64 MiB are rejected with
+ *   KDT_ERR_CAPACITY (about one million 3-D points; fewer in higher d).
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture. Later calls reuse the address.
+ *   All calls on a device share the array: calls that overlap on the GPU (for
+ *   example on two streams) race and produce garbage. Issue them in order.
+ *   Arguments, outputs and errors are those of kdt_build (without workspace).
+ */
+kdt_status kdt_build_noalloc(const float *points, const kdt_params *p, uint32_t *out_perm,
+                             float *out_split_vals, int8_t *out_split_dims,
+                             int64_t *out_node_offsets, int32_t *out_levels, void *stream);
+
 /* Largest cell (points) the in-shared-memory subtree kernel takes for d
  * coordinates; larger cells are split by the multi-CTA level pipeline. */
 int32_t kdt_subtree_capacity(int32_t d);

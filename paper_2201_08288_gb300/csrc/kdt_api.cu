@@ -289,6 +289,24 @@ kdt_status build_device(const float* points, const kdt_params& p, uint8_t* ws, c
 }
 
 }  // namespace
+
+// Build with a caller-provided workspace that is never NULL; used by entry
+// points that own their workspace memory. Allocates nothing.
+kdt_status build_in_workspace(const float* points, const kdt_params* p, void* workspace, size_t workspace_bytes,
+                              uint32_t* out_perm, float* out_split_vals, int8_t* out_split_dims,
+                              int64_t* out_node_offsets, int32_t* out_levels, cudaStream_t st) {
+  const kdt_status v = validate(p);
+  if (v != KDT_OK) return v;
+  if ((p->n > 0 && (!points || !out_perm)) || !out_node_offsets || !workspace) return KDT_ERR_INVALID_ARG;
+  const int L_cap = p->depth > 0 ? p->depth : p->max_levels;
+  if (L_cap > 0 && (!out_split_vals || !out_split_dims)) return KDT_ERR_INVALID_ARG;
+  const Layout L = make_layout(*p);
+  if (workspace_bytes < L.total) return KDT_ERR_CAPACITY;
+  if ((uintptr_t)workspace % kAlign) return KDT_ERR_INVALID_ARG;
+  return build_device(points, *p, (uint8_t*)workspace, L, out_perm, out_split_vals, out_split_dims,
+                      out_node_offsets, out_levels, st);
+}
+
 }  // namespace kdt
 
 using namespace kdt;

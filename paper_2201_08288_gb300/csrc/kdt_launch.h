@@ -64,6 +64,16 @@ void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint
 
 void launch_iota(uint32_t* out, uint32_t n, cudaStream_t st);
 
+}  // namespace kdt
+
+#include "kdt.h"
+
+namespace kdt {
+
+kdt_status build_in_workspace(const float* points, const kdt_params* p, void* workspace, size_t workspace_bytes,
+                              uint32_t* out_perm, float* out_split_vals, int8_t* out_split_dims,
+                              int64_t* out_node_offsets, int32_t* out_levels, cudaStream_t st);
+
 void launch_finalize(const TreeDev* tree, const uint32_t* term_count, uint32_t max_terms, cudaStream_t st);
 
 }  // namespace kdt

@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "KDT_OK", 1: "KDT_ERR_INVALID_ARG", 2: "KDT_ERR_NAN_INPUT", 3
 # Every symbol include/kdt.h declares (checked by the CPU test suite).
 EXPORTED = ["kdt_workspace_size", "kdt_build", "kdt_workspace_size_host", "kdt_build_host",
             "kdt_subtree_capacity", "kdt_status_str", "kdt_trace_enable", "kdt_launch_count",
-            "kdt_trace_read"]
+            "kdt_trace_read", "kdt_build_noalloc"]
 
 
 class KdtError(RuntimeError):
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH):
     lib.kdt_subtree_capacity.restype = ctypes.c_int32
     lib.kdt_status_str.argtypes = [ctypes.c_int]
     lib.kdt_status_str.restype = ctypes.c_char_p
+    lib.kdt_build_noalloc.argtypes = [vp, P, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), vp]
+    lib.kdt_build_noalloc.restype = ctypes.c_int
     lib.kdt_trace_enable.argtypes = [ctypes.c_int32]
     lib.kdt_trace_enable.restype = None
     lib.kdt_launch_count.argtypes = []
@@ -242,6 +244,34 @@ def kdt_build_host(points: np.ndarray, *, r: int = 1, subset_mode: int = KDT_SUB
                                        ctypes.byref(levels), stream.cuda_stream)
     if st:
         raise KdtError(st, "kdt_build_host")
+    L = levels.value
+    m = (1 << L) - 1
+    return Tree(outputs.perm[:n], outputs.split_vals[:m], outputs.split_dims[:m],
+                outputs.node_offsets[:(1 << L) + 1], L)
+
+
+def kdt_build_noalloc(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None, depth: int = 0,
+                      leaf_size: int = 1, max_levels: int = 20, key_rule: int = KDT_KEY_CYCLIC, stream=None,
+                      outputs: Tree) -> Tree:
+    """kdt_build that allocates nothing: the library's fixed 64 MiB device
+    scratch array is the workspace. outputs: preallocated Tree of tensors
+    (sized for the capacity), as for kdt_build."""
+    import torch
+    if not (points.is_cuda and points.dtype == torch.float32 and points.is_contiguous() and points.dim() == 2):
+        raise ValueError("points must be a contiguous float32 CUDA tensor [d, n]")
+    d, n = points.shape
+    sid_ptr, sid_bytes = _sid_info(sid)
+    p = make_params(n, d, r=r, subset_mode=subset_mode, sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth,
+                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule)
+    if stream is None:
+        stream = torch.cuda.current_stream(points.device)
+    levels = ctypes.c_int32(0)
+    st = load_library().kdt_build_noalloc(points.data_ptr(), ctypes.byref(p), outputs.perm.data_ptr(),
+                                          outputs.split_vals.data_ptr(), outputs.split_dims.data_ptr(),
+                                          outputs.node_offsets.data_ptr(), ctypes.byref(levels),
+                                          stream.cuda_stream)
+    if st:
+        raise KdtError(st, "kdt_build_noalloc")
     L = levels.value
     m = (1 << L) - 1
     return Tree(outputs.perm[:n], outputs.split_vals[:m], outputs.split_dims[:m],
