@@ -40,6 +40,8 @@ def workload(name: str, rank: int):
         spec = W.config2()
     elif name == "c1":
         spec = W.config1()
+    elif name == "c3s":  # profiling case: config 3's recipe at n=2^22 (larger than L2, small for ncu)
+        spec = W.config3(n=1 << 22, depth=15)
     else:
         raise SystemExit(f"unknown workload {name}")
     spec.seed += 1000 * rank
@@ -206,7 +208,7 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c3s"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
