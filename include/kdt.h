@@ -138,6 +138,69 @@ kdt_status kdt_build_host(const float *points_host, const kdt_params *p, void *w
                           float *out_split_vals_host, int8_t *out_split_dims_host,
                           int64_t *out_node_offsets_host, int32_t *out_levels, void *stream);
 
+/* ---- batched builds -----------------------------------------------------
+ * Many independent trees (different n, d, r, rules) built together: every
+ * level step runs once over the cells of all trees (each tree at its own
+ * level), and every cell that fits in shared memory is finished by one
+ * persistent launch per step. Each tree's outputs equal its kdt_build outputs
+ * bit for bit. */
+typedef struct kdt_tree_desc {
+  const float *points;         /* device, float32 SoA [d][n] (as kdt_build)              */
+  kdt_params params;           /* per tree; explicit subset ids are device pointers      */
+  uint32_t *out_perm;          /* device outputs, sized as for kdt_build                 */
+  float *out_split_vals;
+  int8_t *out_split_dims;
+  int64_t *out_node_offsets;
+} kdt_tree_desc;
+
+/* Device workspace for kdt_build_batched with these trees. */
+kdt_status kdt_workspace_size_batched(const kdt_tree_desc *trees, int32_t num_trees, size_t *bytes);
+/*
+ * Build num_trees trees. workspace: device, >= kdt_workspace_size_batched
+ * bytes (or NULL: allocated and freed by the call). out_levels, out_status:
+ * host arrays of num_trees (may be NULL) receiving each tree's L and status;
+ * a failing tree (NaN input, level cap) does not stop the others. Returns
+ * KDT_OK when every tree succeeded, else the first tree's error (or a call
+ * error: KDT_ERR_INVALID_ARG, KDT_ERR_CAPACITY, KDT_ERR_OOM, KDT_ERR_CUDA).
+ */
+kdt_status kdt_build_batched(const kdt_tree_desc *trees, int32_t num_trees, void *workspace,
+                             size_t workspace_bytes, int32_t *out_levels, kdt_status *out_status,
+                             void *stream);
+
+/* ---- serving ------------------------------------------------------------
+ * A request loop with continuous batching. The server allocates one device
+ * arena of mem_budget_bytes at creation (its only allocation) and runs a
+ * worker thread. Requests are admitted in arrival order whenever a slot
+ * (max_trees_in_flight), arena memory for the tree's working buffers and
+ * table capacity are free; between two level steps, so a request that
+ * arrives while others are being built joins the next step and its work
+ * overlaps theirs on the device. Points and outputs stay in the caller's
+ * device buffers (they must stay valid until the request completes). A
+ * request's outputs are identical to kdt_build's, alone or in any mix. */
+typedef struct kdt_server kdt_server;
+typedef struct kdt_server_info {
+  uint64_t submitted, admitted, completed, ticks;
+  int32_t in_flight, peak_in_flight;
+  uint64_t arena_bytes, arena_bytes_in_use;
+} kdt_server_info;
+
+/* Create a server on the current device. Errors: KDT_ERR_INVALID_ARG (budget
+ * below 64 MiB, max_trees_in_flight < 1), KDT_ERR_OOM, KDT_ERR_CUDA. */
+kdt_status kdt_server_create(size_t mem_budget_bytes, int32_t max_trees_in_flight, kdt_server **out);
+/* Queue a build. *ticket identifies it. KDT_ERR_CAPACITY: the request can
+ * never fit the budget; KDT_ERR_INVALID_ARG as kdt_build. */
+kdt_status kdt_server_submit(kdt_server *s, const kdt_tree_desc *request, uint64_t *ticket);
+/* Wait up to wait_ms (< 0: forever, 0: do not wait) for a ticket. KDT_OK: the
+ * request finished; *result holds its build status, *levels its L and
+ * *latency_ms the time from submit to completion; the ticket is released.
+ * KDT_ERR_BUSY: not finished yet. KDT_ERR_NOT_FOUND: unknown ticket. */
+kdt_status kdt_server_poll(kdt_server *s, uint64_t ticket, int32_t wait_ms, kdt_status *result,
+                           int32_t *levels, double *latency_ms);
+/* Counters of the server (requests, ticks, occupancy). */
+kdt_status kdt_server_stats(kdt_server *s, kdt_server_info *out);
+/* Finish the requests in flight, drop the queued ones, free the arena. */
+kdt_status kdt_server_destroy(kdt_server *s);
+
 /* ---- tracing ------------------------------------------------------------
  * Every kernel launch of the library is counted. With tracing enabled, each
  * launch is also bracketed by two CUDA events recorded on its stream;

@@ -1,0 +1,382 @@
+// kdt_engine.cu -- the forest engine (see kdt_engine.h).
+#include <algorithm>
+#include <cstring>
+
+#include "kdt_engine.h"
+
+namespace kdt {
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// Engine words.
+enum Word { W_NTILES = 0, W_BIGSEG, W_HEAD, W_NEXTBIG, W_SMALL, W_BIGPTS, W_SMALLPTS, W_COUNT };
+// Per-slot words: [which][max_trees].
+enum SlotWord { S_TERM = 0, S_STATUS, S_LEVELS, S_LIVE, S_COUNT };
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return sms;
+}
+
+kdt_status map_status(int32_t st) {
+  switch (st) {
+    case ST_OK: return KDT_OK;
+    case ST_INVALID_ARG: return KDT_ERR_INVALID_ARG;
+    case ST_NAN_INPUT: return KDT_ERR_NAN_INPUT;
+    case ST_LEVEL_CAP: return KDT_ERR_LEVEL_CAP;
+    case ST_CAPACITY: return KDT_ERR_CAPACITY;
+    case ST_TIMEOUT: return KDT_ERR_TIMEOUT;
+    default: return KDT_ERR_CUDA;
+  }
+}
+
+#define ENGINE_TRY(expr)         \
+  do {                           \
+    if ((expr) != cudaSuccess) { \
+      (void)cudaGetLastError();  \
+      return KDT_ERR_CUDA;       \
+    }                            \
+  } while (0)
+
+}  // namespace
+
+kdt_status validate_params(const kdt_params* p) {
+  if (!p) return KDT_ERR_INVALID_ARG;
+  if (p->n < 0 || p->n > (int64_t)0xffffffffLL) return KDT_ERR_INVALID_ARG;
+  if (p->d < 1 || p->d > KDT_MAX_DIMS) return KDT_ERR_INVALID_ARG;
+  if (p->r < 1 || p->r > KDT_MAX_SUBSETS) return KDT_ERR_INVALID_ARG;
+  if (p->key_rule != KDT_KEY_CYCLIC && p->key_rule != KDT_KEY_WIDEST_SPREAD) return KDT_ERR_INVALID_ARG;
+  if (p->subset_mode != KDT_SUBSET_MOD && p->subset_mode != KDT_SUBSET_CONTIGUOUS &&
+      p->subset_mode != KDT_SUBSET_EXPLICIT)
+    return KDT_ERR_INVALID_ARG;
+  if (p->subset_mode == KDT_SUBSET_EXPLICIT && p->n > 0 &&
+      ((p->subset_id8 == nullptr) == (p->subset_id16 == nullptr)))
+    return KDT_ERR_INVALID_ARG;
+  if (p->depth < 0 || p->depth > KDT_MAX_LEVELS) return KDT_ERR_INVALID_ARG;
+  if (p->depth == 0) {
+    if (p->leaf_size < 1) return KDT_ERR_INVALID_ARG;
+    if (p->max_levels < 0 || p->max_levels > KDT_MAX_LEVELS) return KDT_ERR_INVALID_ARG;
+  }
+  if (p->reserved != 0) return KDT_ERR_INVALID_ARG;
+  return KDT_OK;
+}
+
+TreePlan plan_tree(const kdt_params& p) {
+  TreePlan t;
+  const uint64_t n = (uint64_t)p.n;
+  t.n = n;
+  t.L_cap = p.depth > 0 ? p.depth : p.max_levels;
+  t.small_max = subtree_capacity(p.d);
+  t.sid_bytes = p.subset_mode == KDT_SUBSET_EXPLICIT ? (p.subset_id16 ? 2 : 1) : 0;
+  const uint64_t leaves = (uint64_t)1 << t.L_cap;
+  t.maxB = std::min<uint64_t>(n / (uint64_t)(t.small_max + 1) + 1, leaves);
+  t.cap_small = std::min<uint64_t>(n, leaves) + 1;
+  t.term_cap = leaves + 1;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    const size_t o = off;
+    off += align_up(b);
+    return o;
+  };
+  for (int b = 0; b < 2; ++b) {
+    t.xbuf[b] = take((size_t)p.d * n * 4);
+    t.pbuf[b] = take(n * 4);
+    t.sbuf[b] = take(n * (size_t)t.sid_bytes);
+  }
+  t.keys = take(n * 4);
+  t.terms = take(t.term_cap * sizeof(TermRec));
+  t.bytes = off;
+  return t;
+}
+
+void StepNeeds::add(const kdt_params& p, const TreePlan& tp) {
+  points += tp.n;
+  maxB += tp.maxB;
+  cap_small += tp.cap_small;
+  nseg += tp.maxB * (uint64_t)p.r;
+  max_trees += 1;
+  slice_cells = std::max<uint32_t>(slice_cells, (uint32_t)tp.small_max);
+  widest = widest || p.key_rule == KDT_KEY_WIDEST_SPREAD;
+  max_d = std::max(max_d, (int)p.d);
+}
+
+StepPlan plan_step(const StepNeeds& needs) {
+  StepPlan s;
+  s.needs = needs;
+  const uint64_t clamp = 0xffffffffull;
+  s.maxB = (uint32_t)std::min<uint64_t>(needs.maxB, clamp);
+  s.cap_small = (uint32_t)std::min<uint64_t>(needs.cap_small, clamp);
+  s.max_tiles = (uint32_t)std::min<uint64_t>(needs.points / kTile + needs.maxB + 1, clamp);
+  s.nseg_cap = (uint32_t)std::min<uint64_t>(needs.nseg, clamp);
+  s.bigseg_cap = (uint32_t)std::min<uint64_t>(needs.points / (kSelSmallMax + 1) + 1, clamp);
+  const int sms = device_sms();
+  s.grid_sub = (uint32_t)(sms > 0 ? sms : 148);
+  const uint32_t mt = std::max<uint32_t>(needs.max_trees, 1);
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    const size_t o = off;
+    off += align_up(b);
+    return o;
+  };
+  s.trees = take((size_t)mt * sizeof(TreeDev));
+  s.words = take(W_COUNT * 4);
+  s.slot_words = take((size_t)S_COUNT * mt * 4);
+  s.slots_list = take((size_t)mt * 4);
+  s.big[0] = take((size_t)s.maxB * sizeof(Cell));
+  s.big[1] = take((size_t)s.maxB * sizeof(Cell));
+  s.small = take((size_t)s.cap_small * sizeof(Cell));
+  s.tile_base = take(((size_t)s.maxB + 1) * 4);
+  s.seg_base = take(((size_t)s.maxB + 1) * 4);
+  s.tiles = take((size_t)s.max_tiles * sizeof(uint2));
+  s.tile_left = take((size_t)s.max_tiles * 4);
+  s.tile_loff = take((size_t)s.max_tiles * 4);
+  s.tile_mm = take(needs.widest ? (size_t)s.max_tiles * 2 * kMaxDims * 2 * 4 : 0);
+  s.child_mm = take(needs.widest ? (size_t)s.maxB * 2 * kMaxDims * 2 * 4 : 0);
+  s.kdim = take((size_t)s.maxB * 4);
+  s.mkey = take((size_t)s.maxB * 4);
+  s.lcount = take((size_t)s.maxB * 4);
+  s.seg_w = take((size_t)s.nseg_cap * 4);
+  s.seg_beg = take((size_t)s.nseg_cap * 4);
+  s.seg_cur = take((size_t)s.nseg_cap * 4);
+  s.seg_med = take((size_t)s.nseg_cap * 4);
+  s.seg_cell = take((size_t)s.nseg_cap * 4);
+  s.bigseg = take((size_t)s.bigseg_cap * 4);
+  s.slices = take((size_t)s.grid_sub * 2 * needs.slice_cells * sizeof(LCell));
+  s.bytes = off;
+  return s;
+}
+
+Engine::Engine(const StepPlan& plan, uint8_t* base, cudaStream_t st) : plan_(plan), base_(base), st_(st) {
+  trees_ = (TreeDev*)(base + plan.trees);
+  words_ = (uint32_t*)(base + plan.words);
+  slot_words_ = (uint32_t*)(base + plan.slot_words);
+  slots_list_ = (uint32_t*)(base + plan.slots_list);
+  big_[0] = (Cell*)(base + plan.big[0]);
+  big_[1] = (Cell*)(base + plan.big[1]);
+  small_ = (Cell*)(base + plan.small);
+  slices_ = (LCell*)(base + plan.slices);
+  s_.tile_base = (uint32_t*)(base + plan.tile_base);
+  s_.seg_base = (uint32_t*)(base + plan.seg_base);
+  s_.tiles = (uint2*)(base + plan.tiles);
+  s_.ntiles_total = words_ + W_NTILES;
+  s_.kdim = (uint32_t*)(base + plan.kdim);
+  s_.mkey = (uint32_t*)(base + plan.mkey);
+  s_.lcount = (uint32_t*)(base + plan.lcount);
+  s_.tile_mm = (uint32_t*)(base + plan.tile_mm);
+  s_.child_mm = (uint32_t*)(base + plan.child_mm);
+  s_.seg_w = (uint32_t*)(base + plan.seg_w);
+  s_.seg_beg = (uint32_t*)(base + plan.seg_beg);
+  s_.seg_cur = (uint32_t*)(base + plan.seg_cur);
+  s_.seg_med = (uint32_t*)(base + plan.seg_med);
+  s_.seg_cell = (uint32_t*)(base + plan.seg_cell);
+  s_.bigseg = (uint32_t*)(base + plan.bigseg);
+  s_.bigseg_count = words_ + W_BIGSEG;
+  s_.tile_left = (uint32_t*)(base + plan.tile_left);
+  s_.tile_loff = (uint32_t*)(base + plan.tile_loff);
+  s_.next_big_count = words_ + W_NEXTBIG;
+  s_.small = small_;
+  s_.small_count = words_ + W_SMALL;
+  s_.small_cap = plan.cap_small;
+  s_.next_big_cap = plan.maxB;
+  s_.next_big_points = words_ + W_BIGPTS;
+  s_.small_points = words_ + W_SMALLPTS;
+}
+
+kdt_status Engine::reset() {
+  ENGINE_TRY(prepare_subtree_kernel());
+  const uint32_t mt = std::max<uint32_t>(plan_.needs.max_trees, 1);
+  ENGINE_TRY(cudaMemsetAsync(words_, 0, W_COUNT * 4, st_));
+  ENGINE_TRY(cudaMemsetAsync(slot_words_, 0, (size_t)S_COUNT * mt * 4, st_));
+  cur_ = 0;
+  big_count_ = small_count_ = 0;
+  big_points_ = small_points_ = 0;
+  root_dims_ = false;
+  pending_big_.clear();
+  pending_small_.clear();
+  return KDT_OK;
+}
+
+kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p, const TreePlan& tp,
+                         uint8_t* tb, uint32_t* out_perm, float* out_vals, int8_t* out_dims, int64_t* out_offs) {
+  const uint32_t mt = std::max<uint32_t>(plan_.needs.max_trees, 1);
+  if (slot >= mt) return KDT_ERR_CAPACITY;
+  TreeDev h{};
+  h.n = p.n;
+  h.d = p.d;
+  h.r = p.r;
+  h.subset_mode = p.subset_mode;
+  h.key_rule = p.key_rule;
+  h.depth = p.depth;
+  h.leaf_size = p.leaf_size;
+  h.max_levels = p.max_levels;
+  h.stall_limit = p.key_rule == KDT_KEY_CYCLIC ? p.d : 1;
+  h.sid_bytes = tp.sid_bytes;
+  h.small_max = tp.small_max;
+  h.x_in = points;
+  h.sid_in = p.subset_id16 ? (const void*)p.subset_id16 : (const void*)p.subset_id8;
+  for (int b = 0; b < 2; ++b) {
+    h.xbuf[b] = (float*)(tb + tp.xbuf[b]);
+    h.pbuf[b] = (uint32_t*)(tb + tp.pbuf[b]);
+    h.sbuf[b] = (void*)(tb + tp.sbuf[b]);
+  }
+  h.keys = (uint32_t*)(tb + tp.keys);
+  h.out_perm = out_perm;
+  h.out_vals = out_vals;
+  h.out_dims = out_dims;
+  h.out_offs = out_offs;
+  h.terms = (TermRec*)(tb + tp.terms);
+  h.term_cap = (uint32_t)std::min<uint64_t>(tp.term_cap, 0xffffffffull);
+  h.term_count = slot_words_ + (size_t)S_TERM * mt + slot;
+  h.status = (int32_t*)(slot_words_ + (size_t)S_STATUS * mt + slot);
+  h.levels = (int32_t*)(slot_words_ + (size_t)S_LEVELS * mt + slot);
+  h.live = (int32_t*)(slot_words_ + (size_t)S_LIVE * mt + slot);
+  ENGINE_TRY(cudaMemcpyAsync(trees_ + slot, &h, sizeof(h), cudaMemcpyHostToDevice, st_));
+  for (int w = 0; w < S_COUNT; ++w)
+    ENGINE_TRY(cudaMemsetAsync(slot_words_ + (size_t)w * mt + slot, 0, 4, st_));
+
+  const uint64_t n = (uint64_t)p.n;
+  const Cell root{0u, (uint32_t)n, 0u, (int32_t)slot, 0, 0, -1};
+  const bool root_terminal = p.depth > 0 ? (n == 0) : (n <= (uint64_t)p.leaf_size);
+  if (root_terminal) {
+    const TermRec tr{0u, (uint32_t)n, 0u, 0};
+    const uint32_t one = 1;
+    ENGINE_TRY(cudaMemcpyAsync(h.terms, &tr, sizeof(tr), cudaMemcpyHostToDevice, st_));
+    ENGINE_TRY(cudaMemcpyAsync(h.term_count, &one, 4, cudaMemcpyHostToDevice, st_));
+    launch_iota(out_perm, (uint32_t)n, st_);
+    ENGINE_TRY(cudaGetLastError());
+    return KDT_OK;
+  }
+  const int32_t one = 1;
+  ENGINE_TRY(cudaMemcpyAsync(h.live, &one, 4, cudaMemcpyHostToDevice, st_));
+  if (n <= (uint64_t)tp.small_max) {
+    pending_small_.push_back(root);
+  } else {
+    pending_big_.push_back(root);
+    if (p.key_rule == KDT_KEY_WIDEST_SPREAD) root_dims_ = true;
+  }
+  return KDT_OK;
+}
+
+kdt_status Engine::tick() {
+  // new roots join the lists of this tick
+  if (!pending_big_.empty()) {
+    if (big_count_ + pending_big_.size() > plan_.maxB) return KDT_ERR_CAPACITY;
+    ENGINE_TRY(cudaMemcpyAsync(big_[cur_] + big_count_, pending_big_.data(), pending_big_.size() * sizeof(Cell),
+                               cudaMemcpyHostToDevice, st_));
+    for (const Cell& c : pending_big_) big_points_ += c.count;
+    big_count_ += (uint32_t)pending_big_.size();
+    pending_big_.clear();
+  }
+  if (!pending_small_.empty()) {
+    if (small_count_ + pending_small_.size() > plan_.cap_small) return KDT_ERR_CAPACITY;
+    ENGINE_TRY(cudaMemcpyAsync(small_ + small_count_, pending_small_.data(),
+                               pending_small_.size() * sizeof(Cell), cudaMemcpyHostToDevice, st_));
+    for (const Cell& c : pending_small_) small_points_ += c.count;
+    small_count_ += (uint32_t)pending_small_.size();
+    pending_small_.clear();
+  }
+  const uint32_t sw[2] = {small_count_, (uint32_t)small_points_};
+  ENGINE_TRY(cudaMemcpyAsync(words_ + W_SMALL, sw, 8, cudaMemcpyHostToDevice, st_));
+
+  if (big_count_ > 0) {
+    ENGINE_TRY(cudaMemsetAsync(words_ + W_NEXTBIG, 0, 4, st_));
+    ENGINE_TRY(cudaMemsetAsync(words_ + W_BIGPTS, 0, 4, st_));
+    s_.cells = big_[cur_];
+    s_.ncells = big_count_;
+    s_.next_big = big_[cur_ ^ 1];
+    const uint64_t nseg_bound = std::min<uint64_t>((uint64_t)big_count_ * KDT_MAX_SUBSETS, plan_.nseg_cap);
+    launch_big_step(trees_, s_, plan_.max_tiles, (uint32_t)nseg_bound, plan_.bigseg_cap, root_dims_,
+                    plan_.needs.widest, plan_.needs.max_d, big_points_, st_);
+    ENGINE_TRY(cudaGetLastError());
+    root_dims_ = false;
+    uint32_t counts[4];
+    ENGINE_TRY(cudaMemcpyAsync(counts, words_ + W_NEXTBIG, 16, cudaMemcpyDeviceToHost, st_));
+    ENGINE_TRY(cudaStreamSynchronize(st_));
+    big_count_ = std::min(counts[0], plan_.maxB);
+    small_count_ = std::min(counts[1], plan_.cap_small);
+    big_points_ = counts[2];
+    small_points_ = counts[3];
+    cur_ ^= 1;
+  } else {
+    big_count_ = 0;
+    big_points_ = 0;
+  }
+  if (small_count_ > 0) {
+    launch_subtree(trees_, small_, small_count_, words_ + W_HEAD, slices_, plan_.needs.slice_cells,
+                   std::min(plan_.grid_sub, small_count_), small_points_, st_);
+    ENGINE_TRY(cudaGetLastError());
+    small_count_ = 0;
+    small_points_ = 0;
+  }
+  return KDT_OK;
+}
+
+kdt_status Engine::done_slots(const std::vector<uint32_t>& slots, std::vector<uint32_t>* done) {
+  const uint32_t mt = std::max<uint32_t>(plan_.needs.max_trees, 1);
+  std::vector<int32_t> live(mt);
+  ENGINE_TRY(cudaMemcpyAsync(live.data(), slot_words_ + (size_t)S_LIVE * mt, (size_t)mt * 4,
+                             cudaMemcpyDeviceToHost, st_));
+  ENGINE_TRY(cudaStreamSynchronize(st_));
+  done->clear();
+  for (uint32_t s : slots)
+    if (s < mt && live[s] <= 0) done->push_back(s);
+  return KDT_OK;
+}
+
+kdt_status Engine::finalize(const std::vector<uint32_t>& slots, std::vector<kdt_status>* status,
+                            std::vector<int32_t>* levels) {
+  const uint32_t mt = std::max<uint32_t>(plan_.needs.max_trees, 1);
+  status->assign(slots.size(), KDT_OK);
+  levels->assign(slots.size(), 0);
+  if (slots.empty()) return KDT_OK;
+  // trees with an error get no finalize (their outputs are undefined)
+  std::vector<int32_t> st(mt), lv(mt);
+  std::vector<uint32_t> tc(mt);
+  ENGINE_TRY(cudaMemcpyAsync(tc.data(), slot_words_ + (size_t)S_TERM * mt, (size_t)mt * 4,
+                             cudaMemcpyDeviceToHost, st_));
+  ENGINE_TRY(cudaMemcpyAsync(st.data(), slot_words_ + (size_t)S_STATUS * mt, (size_t)mt * 4,
+                             cudaMemcpyDeviceToHost, st_));
+  ENGINE_TRY(cudaMemcpyAsync(lv.data(), slot_words_ + (size_t)S_LEVELS * mt, (size_t)mt * 4,
+                             cudaMemcpyDeviceToHost, st_));
+  ENGINE_TRY(cudaStreamSynchronize(st_));
+  std::vector<uint32_t> ok;
+  uint32_t max_rec = 0;
+  for (uint32_t s : slots)
+    if (st[s] == ST_OK) {
+      ok.push_back(s);
+      max_rec = std::max(max_rec, tc[s]);
+    }
+  if (!ok.empty()) {
+    ENGINE_TRY(cudaMemcpyAsync(slots_list_, ok.data(), ok.size() * 4, cudaMemcpyHostToDevice, st_));
+    launch_finalize_many(trees_, slots_list_, (uint32_t)ok.size(), max_rec, st_);
+    ENGINE_TRY(cudaGetLastError());
+    ENGINE_TRY(cudaStreamSynchronize(st_));
+  }
+  for (size_t i = 0; i < slots.size(); ++i) {
+    (*status)[i] = map_status(st[slots[i]]);
+    (*levels)[i] = lv[slots[i]];
+  }
+  return KDT_OK;
+}
+
+kdt_status Engine::run_to_completion() {
+  for (int guard = 0; busy() || !pending_big_.empty() || !pending_small_.empty(); ++guard) {
+    if (guard > 2 * KDT_MAX_LEVELS + 4) return KDT_ERR_CUDA;
+    const kdt_status s = tick();
+    if (s != KDT_OK) return s;
+  }
+  return KDT_OK;
+}
+
+}  // namespace kdt

@@ -1,0 +1,99 @@
+// kdt_engine.h -- host-side driver shared by the plain, batched and served
+// builds.
+//
+// The engine owns the tables of one "forest": up to max_trees trees, each in
+// its own slot, whose cells are split together. One tick is one level step of
+// the multi-CTA pipeline over every big cell of every tree in flight (each
+// tree at its own level), followed by the subtree kernel over every cell that
+// became small during the tick. A tree's cells never mix with another tree's
+// data; trees join (admit) and leave (finalize) between ticks.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kdt.h"
+#include "kdt_launch.h"
+
+namespace kdt {
+
+kdt_status validate_params(const kdt_params* p);
+
+// Memory of one tree (offsets relative to the tree's base, 256-byte aligned).
+struct TreePlan {
+  int L_cap = 0;
+  int small_max = 0;
+  int sid_bytes = 0;
+  uint64_t n = 0;
+  uint64_t term_cap = 0;
+  uint64_t maxB = 0;      // big cells at one level
+  uint64_t cap_small = 0; // small cells over the whole build
+  size_t xbuf[2] = {0, 0}, pbuf[2] = {0, 0}, sbuf[2] = {0, 0}, keys = 0, terms = 0;
+  size_t bytes = 0;
+};
+TreePlan plan_tree(const kdt_params& p);
+
+// Capacities of the shared tables, accumulated over the trees they must serve
+// at the same time.
+struct StepNeeds {
+  uint64_t points = 0, maxB = 0, cap_small = 0, nseg = 0;
+  uint32_t max_trees = 0, slice_cells = 32;
+  bool widest = false;
+  int max_d = 1;
+  void add(const kdt_params& p, const TreePlan& tp);
+};
+
+struct StepPlan {
+  StepNeeds needs;
+  uint32_t maxB = 0, cap_small = 0, max_tiles = 0, nseg_cap = 0, bigseg_cap = 0, grid_sub = 0;
+  size_t trees = 0, words = 0, slot_words = 0, slots_list = 0, big[2] = {0, 0}, small = 0, tile_base = 0,
+         seg_base = 0, tiles = 0, tile_left = 0, tile_loff = 0, tile_mm = 0, child_mm = 0, kdim = 0,
+         mkey = 0, lcount = 0, seg_w = 0, seg_beg = 0, seg_cur = 0, seg_med = 0, seg_cell = 0,
+         bigseg = 0, slices = 0;
+  size_t bytes = 0;
+};
+StepPlan plan_step(const StepNeeds& needs);
+
+class Engine {
+ public:
+  Engine(const StepPlan& plan, uint8_t* base, cudaStream_t st);
+
+  // Clear every counter (call once before the first admit).
+  kdt_status reset();
+  // Put a tree into `slot`. tree_base holds TreePlan::bytes of device memory.
+  kdt_status admit(uint32_t slot, const float* points, const kdt_params& p, const TreePlan& tp, uint8_t* tree_base,
+                   uint32_t* out_perm, float* out_vals, int8_t* out_dims, int64_t* out_offs);
+  // One tick (see above). Synchronises the stream once.
+  kdt_status tick();
+  // True while some cell of some tree still waits for a tick.
+  bool busy() const { return big_count_ > 0 || small_count_ > 0; }
+  // Slots (among `slots`) whose trees have no cell left.
+  kdt_status done_slots(const std::vector<uint32_t>& slots, std::vector<uint32_t>* done);
+  // Offsets and sentinels of finished trees, then their status and L.
+  kdt_status finalize(const std::vector<uint32_t>& slots, std::vector<kdt_status>* status,
+                      std::vector<int32_t>* levels);
+  // Run ticks until nothing is left in flight.
+  kdt_status run_to_completion();
+
+ private:
+  StepPlan plan_;
+  uint8_t* base_;
+  cudaStream_t st_;
+  TreeDev* trees_ = nullptr;      // device [max_trees]
+  uint32_t* words_ = nullptr;     // device engine words
+  uint32_t* slot_words_ = nullptr;  // device [4][max_trees]: term_count, status, levels, live
+  uint32_t* slots_list_ = nullptr;  // device [max_trees]
+  Cell* big_[2] = {nullptr, nullptr};
+  Cell* small_ = nullptr;
+  LCell* slices_ = nullptr;
+  StepDev s_{};
+  int cur_ = 0;
+  uint32_t big_count_ = 0, small_count_ = 0;
+  uint64_t big_points_ = 0, small_points_ = 0;
+  bool root_dims_ = false;
+  std::vector<Cell> pending_big_, pending_small_;
+};
+
+}  // namespace kdt

@@ -71,6 +71,7 @@ struct TreeDev {
   uint32_t* term_count;
   int32_t* status;
   int32_t* levels;       // L (max terminal level in leaf mode)
+  int32_t* live;         // cells of this tree still waiting to be split (0: the tree is done)
 };
 
 // A cell of the tree: a contiguous position range [begin, begin+count) of its

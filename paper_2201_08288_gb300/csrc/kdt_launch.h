@@ -74,6 +74,8 @@ kdt_status build_in_workspace(const float* points, const kdt_params* p, void* wo
                               uint32_t* out_perm, float* out_split_vals, int8_t* out_split_dims,
                               int64_t* out_node_offsets, int32_t* out_levels, cudaStream_t st);
 
+void launch_finalize_many(const TreeDev* trees, const uint32_t* slots, uint32_t nslots, uint32_t max_records,
+                          cudaStream_t st);
 void launch_finalize(const TreeDev* tree, const uint32_t* term_count, uint32_t max_terms, cudaStream_t st);
 
 }  // namespace kdt

@@ -18,6 +18,8 @@
 // Work is split into tiles of kTile points of one cell; a thread owns kItems
 // points of a tile (strided by the block size, so every load is coalesced)
 // and issues all of its loads before it uses any of them.
+#include <algorithm>
+
 #include "kdt_internal.cuh"
 #include "kdt_launch.h"
 #include "kdt_trace.h"
@@ -349,22 +351,24 @@ __device__ __forceinline__ uint32_t warp_rank_median(const uint32_t* keys, uint3
   return __shfl_sync(0xffffffffu, k, __ffs(hit) - 1);
 }
 
-// One warp per segment of at most kSelSmallMax points.
-__global__ void __launch_bounds__(256) k_select_small(const TreeDev* trees, StepDev s, uint32_t nseg) {
+// One warp per segment of at most kSelSmallMax points; warps stride over the
+// segments of the step (their number is read from the device).
+__global__ void __launch_bounds__(256) k_select_small(const TreeDev* trees, StepDev s) {
   __shared__ uint32_t hist[8][256];
   const int warp = threadIdx.x >> 5;
-  const uint32_t g = blockIdx.x * 8u + (uint32_t)warp;
-  if (g >= nseg) return;
-  const uint32_t w = s.seg_w[g];
-  if (w == 0 || w > (uint32_t)kSelSmallMax) return;
-  const Cell cell = s.cells[s.seg_cell[g]];
-  const uint32_t* keys = trees[cell.tree].keys + s.seg_beg[g];
-  uint32_t med;
-  if (w <= 32)
-    med = warp_rank_median(keys, w);
-  else
-    med = warp_radix_select(keys, w, (w - 1) / 2, hist[warp]);
-  if ((threadIdx.x & 31) == 0) s.seg_med[g] = med;
+  const uint32_t nseg = s.seg_base[s.ncells];
+  for (uint32_t g = blockIdx.x * 8u + (uint32_t)warp; g < nseg; g += gridDim.x * 8u) {
+    const uint32_t w = s.seg_w[g];
+    if (w == 0 || w > (uint32_t)kSelSmallMax) continue;
+    const Cell cell = s.cells[s.seg_cell[g]];
+    const uint32_t* keys = trees[cell.tree].keys + s.seg_beg[g];
+    uint32_t med;
+    if (w <= 32)
+      med = warp_rank_median(keys, w);
+    else
+      med = warp_radix_select(keys, w, (w - 1) / 2, hist[warp]);
+    if ((threadIdx.x & 31) == 0) s.seg_med[g] = med;
+  }
 }
 
 // One CTA per listed large segment: the same radix select with a CTA-wide
@@ -717,6 +721,7 @@ __global__ void k_next(const TreeDev* trees, StepDev s) {
   const int stall = (R == 0) ? cell.stall + 1 : 0;
   const uint32_t cb[2] = {cell.begin, cell.begin + L};
   const uint32_t cc[2] = {L, R};
+  int live_delta = -1;  // this cell is done; each child that still needs splitting adds one
   for (int side = 0; side < 2; ++side) {
     const uint32_t heap = 2u * cell.heap + 1u + (uint32_t)side;
     if (is_terminal(t, cc[side], level, stall)) {
@@ -727,6 +732,7 @@ __global__ void k_next(const TreeDev* trees, StepDev s) {
       set_status(t, ST_LEVEL_CAP);
       continue;
     }
+    ++live_delta;
     int16_t dim = -1;
     if (t.key_rule == KEY_WIDEST) {
       int best = 0;
@@ -752,6 +758,7 @@ __global__ void k_next(const TreeDev* trees, StepDev s) {
       atomicAdd(s.next_big_points, cc[side]);
     }
   }
+  if (live_delta) atomicAdd(t.live, live_delta);
 }
 
 }  // namespace
@@ -774,7 +781,7 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
   { TraceScope ts(K_GROUP, st, points); k_group<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
   {
     TraceScope ts(K_SELECT_SMALL, st, points);
-    k_select_small<<<(nseg + 7) / 8, 256, 0, st>>>(trees, s, nseg);
+    k_select_small<<<std::min<uint32_t>((nseg + 7) / 8, 152u * 32u), 256, 0, st>>>(trees, s);
   }
   if (max_bigseg) { TraceScope ts(K_SELECT_BIG, st); k_select_big<<<max_bigseg, 256, 0, st>>>(trees, s); }
   { TraceScope ts(K_COMBINE, st); k_combine<<<nc, 256, 0, st>>>(trees, s); }

@@ -586,6 +586,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
 
     // ---- write the permutation in final order
     for (uint32_t i = tid; i < N; i += T) t.out_perm[(int64_t)c.begin + i] = pm[ordA[i]];
+    if (tid == 0) atomicSub(t.live, 1);
   }
 }
 
@@ -617,6 +618,37 @@ __global__ void k_finalize(const TreeDev* tree, const uint32_t* term_count) {
   }
 }
 
+// Finalize of several trees: grid (chunks, trees); each warp takes terminal
+// records of its tree in turn (same per-record work as k_finalize).
+__global__ void k_finalize_many(const TreeDev* trees, const uint32_t* slots, uint32_t nslots) {
+  const uint32_t si = blockIdx.y;
+  if (si >= nslots) return;
+  const TreeDev& t = trees[slots[si]];
+  const uint32_t nrec = min(*t.term_count, t.term_cap);
+  const int L = t.depth > 0 ? t.depth : *t.levels;
+  const int lane = threadIdx.x & 31;
+  const uint32_t wpb = blockDim.x >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) t.out_offs[(int64_t)1 << L] = t.n;
+  for (uint32_t rec = blockIdx.x * wpb + (threadIdx.x >> 5); rec < nrec; rec += gridDim.x * wpb) {
+    const TermRec tr = t.terms[rec];
+    const int lv = tr.level;
+    if (lv > L) continue;
+    const int64_t k = (int64_t)tr.heap - (((int64_t)1 << lv) - 1);
+    const int64_t span = (int64_t)1 << (L - lv);
+    const int64_t leaf0 = k * span;
+    for (int64_t j = lane; j < span; j += 32)
+      t.out_offs[leaf0 + j] = (j == 0) ? (int64_t)tr.begin : (int64_t)tr.begin + tr.count;
+    for (int l2 = lv; l2 < L; ++l2) {
+      const int64_t width = (int64_t)1 << (l2 - lv);
+      const int64_t first = ((int64_t)tr.heap + 1) * width - 1;
+      for (int64_t j = lane; j < width; j += 32) {
+        t.out_dims[first + j] = -1;
+        t.out_vals[first + j] = __int_as_float(0x7f800000);
+      }
+    }
+  }
+}
+
 __global__ void k_iota(uint32_t* out, uint32_t n) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = i;
 }
@@ -640,6 +672,14 @@ void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint
   cudaMemsetAsync(head, 0, sizeof(uint32_t), st);
   TraceScope ts(K_SUBTREE, st, points);
   k_subtree<<<grid, T, kSubtreeSmemBytes, st>>>(trees, list, count, head, slices, slice_cells);
+}
+
+void launch_finalize_many(const TreeDev* trees, const uint32_t* slots, uint32_t nslots, uint32_t max_records,
+                          cudaStream_t st) {
+  if (nslots == 0) return;
+  TraceScope ts(K_FINALIZE, st);
+  const uint32_t chunks = std::max<uint32_t>(1, std::min<uint32_t>((max_records + 7) / 8, 8192));
+  k_finalize_many<<<dim3(chunks, nslots), 256, 0, st>>>(trees, slots, nslots);
 }
 
 void launch_finalize(const TreeDev* tree, const uint32_t* term_count, uint32_t max_terms, cudaStream_t st) {

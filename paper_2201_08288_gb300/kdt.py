@@ -32,7 +32,9 @@ STATUS_NAMES = {0: "KDT_OK", 1: "KDT_ERR_INVALID_ARG", 2: "KDT_ERR_NAN_INPUT", 3
 # Every symbol include/kdt.h declares (checked by the CPU test suite).
 EXPORTED = ["kdt_workspace_size", "kdt_build", "kdt_workspace_size_host", "kdt_build_host",
             "kdt_subtree_capacity", "kdt_status_str", "kdt_trace_enable", "kdt_launch_count",
-            "kdt_trace_read", "kdt_build_noalloc"]
+            "kdt_trace_read", "kdt_build_noalloc", "kdt_workspace_size_batched", "kdt_build_batched",
+            "kdt_server_create", "kdt_server_submit", "kdt_server_poll", "kdt_server_stats",
+            "kdt_server_destroy"]
 
 
 class KdtError(RuntimeError):
@@ -62,6 +64,23 @@ class kdt_params(ctypes.Structure):
     ]
 
 
+class kdt_tree_desc(ctypes.Structure):
+    _fields_ = [
+        ("points", ctypes.c_void_p),
+        ("params", kdt_params),
+        ("out_perm", ctypes.c_void_p),
+        ("out_split_vals", ctypes.c_void_p),
+        ("out_split_dims", ctypes.c_void_p),
+        ("out_node_offsets", ctypes.c_void_p),
+    ]
+
+
+class kdt_server_info(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("ticks", ctypes.c_uint64), ("in_flight", ctypes.c_int32), ("peak_in_flight", ctypes.c_int32),
+                ("arena_bytes", ctypes.c_uint64), ("arena_bytes_in_use", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -87,6 +106,23 @@ def load_library(path: str = LIB_PATH):
     lib.kdt_subtree_capacity.restype = ctypes.c_int32
     lib.kdt_status_str.argtypes = [ctypes.c_int]
     lib.kdt_status_str.restype = ctypes.c_char_p
+    D = ctypes.POINTER(kdt_tree_desc)
+    lib.kdt_workspace_size_batched.argtypes = [D, ctypes.c_int32, ctypes.POINTER(sz)]
+    lib.kdt_workspace_size_batched.restype = ctypes.c_int
+    lib.kdt_build_batched.argtypes = [D, ctypes.c_int32, vp, sz, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int), vp]
+    lib.kdt_build_batched.restype = ctypes.c_int
+    lib.kdt_server_create.argtypes = [sz, ctypes.c_int32, ctypes.POINTER(vp)]
+    lib.kdt_server_create.restype = ctypes.c_int
+    lib.kdt_server_submit.argtypes = [vp, D, ctypes.POINTER(ctypes.c_uint64)]
+    lib.kdt_server_submit.restype = ctypes.c_int
+    lib.kdt_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+    lib.kdt_server_poll.restype = ctypes.c_int
+    lib.kdt_server_stats.argtypes = [vp, ctypes.POINTER(kdt_server_info)]
+    lib.kdt_server_stats.restype = ctypes.c_int
+    lib.kdt_server_destroy.argtypes = [vp]
+    lib.kdt_server_destroy.restype = ctypes.c_int
     lib.kdt_build_noalloc.argtypes = [vp, P, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), vp]
     lib.kdt_build_noalloc.restype = ctypes.c_int
     lib.kdt_trace_enable.argtypes = [ctypes.c_int32]
@@ -276,3 +312,137 @@ def kdt_build_noalloc(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, 
     m = (1 << L) - 1
     return Tree(outputs.perm[:n], outputs.split_vals[:m], outputs.split_dims[:m],
                 outputs.node_offsets[:(1 << L) + 1], L)
+
+
+def _alloc_outputs(n: int, cap: int, dev):
+    import torch
+    return Tree(torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+                torch.empty(max((1 << cap) - 1, 1), dtype=torch.float32, device=dev),
+                torch.empty(max((1 << cap) - 1, 1), dtype=torch.int8, device=dev),
+                torch.empty((1 << cap) + 1, dtype=torch.int64, device=dev), 0)
+
+
+def make_descs(items, outputs=None):
+    """items: sequence of dicts with keys points (CUDA float32 [d, n]), and optionally
+    sid, r, subset_mode, depth, leaf_size, max_levels, key_rule. Returns the
+    ctypes descriptor array and the output Trees (allocated if not given)."""
+    descs = (kdt_tree_desc * len(items))()
+    outs = []
+    for i, it in enumerate(items):
+        pts = it["points"]
+        d, n = pts.shape
+        sid_ptr, sid_bytes = _sid_info(it.get("sid"))
+        depth = it.get("depth", 0)
+        max_levels = it.get("max_levels", 20)
+        p = make_params(n, d, r=it.get("r", 1), subset_mode=it.get("subset_mode", KDT_SUBSET_MOD),
+                        sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth, leaf_size=it.get("leaf_size", 1),
+                        max_levels=max_levels, key_rule=it.get("key_rule", KDT_KEY_CYCLIC))
+        o = outputs[i] if outputs is not None else _alloc_outputs(n, _capacity(depth, max_levels), pts.device)
+        outs.append(o)
+        descs[i].points = pts.data_ptr()
+        descs[i].params = p
+        descs[i].out_perm = o.perm.data_ptr()
+        descs[i].out_split_vals = o.split_vals.data_ptr()
+        descs[i].out_split_dims = o.split_dims.data_ptr()
+        descs[i].out_node_offsets = o.node_offsets.data_ptr()
+    return descs, outs
+
+
+def kdt_workspace_size_batched(descs) -> int:
+    out = ctypes.c_size_t(0)
+    st = load_library().kdt_workspace_size_batched(descs, len(descs), ctypes.byref(out))
+    if st:
+        raise KdtError(st, "kdt_workspace_size_batched")
+    return out.value
+
+
+def kdt_build_batched(items, *, workspace=None, stream=None, outputs=None, descs=None):
+    """Build many trees together. Returns (trees, statuses): per item a Tree of
+    output tensors sliced to its L (None where its status is not 0) and the
+    per-tree status codes."""
+    import torch
+    if descs is None:
+        descs, outs = make_descs(items, outputs)
+    else:
+        outs = outputs
+    num = len(descs)
+    levels = (ctypes.c_int32 * num)()
+    stats = (ctypes.c_int * num)()
+    ws_ptr, ws_bytes = 0, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = load_library().kdt_build_batched(descs, num, ws_ptr or None, ws_bytes, levels, stats, stream.cuda_stream)
+    if st and not any(stats[i] for i in range(num)):
+        raise KdtError(st, "kdt_build_batched")
+    trees = []
+    for i in range(num):
+        if stats[i]:
+            trees.append(None)
+            continue
+        L = levels[i]
+        n = descs[i].params.n
+        m = (1 << L) - 1
+        o = outs[i]
+        trees.append(Tree(o.perm[:n], o.split_vals[:m], o.split_dims[:m], o.node_offsets[:(1 << L) + 1], L))
+    return trees, [int(stats[i]) for i in range(num)]
+
+
+class Server:
+    """Continuous-batching build server (kdt_server_*). Requests are dicts as
+    for kdt_build_batched; the caller keeps the tensors alive until poll
+    returns."""
+
+    def __init__(self, mem_budget_bytes: int, max_trees_in_flight: int = 256):
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        st = self._lib.kdt_server_create(mem_budget_bytes, max_trees_in_flight, ctypes.byref(self._h))
+        if st:
+            raise KdtError(st, "kdt_server_create")
+        self._keep = {}
+
+    def submit(self, item, outputs=None) -> int:
+        descs, outs = make_descs([item], [outputs] if outputs is not None else None)
+        t = ctypes.c_uint64(0)
+        st = self._lib.kdt_server_submit(self._h, descs, ctypes.byref(t))
+        if st:
+            raise KdtError(st, "kdt_server_submit")
+        self._keep[t.value] = (item, outs[0], descs)
+        return t.value
+
+    def poll(self, ticket: int, wait_ms: int = -1):
+        """(status, Tree or None, latency_ms), or None if not finished yet."""
+        res, lv, lat = ctypes.c_int(0), ctypes.c_int32(0), ctypes.c_double(0)
+        st = self._lib.kdt_server_poll(self._h, ticket, wait_ms, ctypes.byref(res), ctypes.byref(lv),
+                                       ctypes.byref(lat))
+        if st == 8:
+            return None
+        if st:
+            raise KdtError(st, "kdt_server_poll")
+        item, o, descs = self._keep.pop(ticket)
+        tree = None
+        if res.value == 0:
+            L = lv.value
+            n = descs[0].params.n
+            m = (1 << L) - 1
+            tree = Tree(o.perm[:n], o.split_vals[:m], o.split_dims[:m], o.node_offsets[:(1 << L) + 1], L)
+        return res.value, tree, lat.value
+
+    def stats(self) -> dict:
+        info = kdt_server_info()
+        st = self._lib.kdt_server_stats(self._h, ctypes.byref(info))
+        if st:
+            raise KdtError(st, "kdt_server_stats")
+        return {k: getattr(info, k) for k, _ in kdt_server_info._fields_}
+
+    def close(self):
+        if self._h:
+            self._lib.kdt_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

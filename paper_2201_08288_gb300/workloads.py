@@ -198,6 +198,12 @@ def config3(n: int = 1 << 27, depth: int = 20) -> TreeSpec:
                     256, 2, 1, depth=depth, sid_seed=1)
 
 
+def leaf_mode_levels(n: int) -> int:
+    """Output capacity (levels) requested for a leaf-mode tree of n points:
+    two levels more than a perfectly balanced tree down to one point."""
+    return int(min(30, max(4, int(np.ceil(np.log2(max(n, 2)))) + 2)))
+
+
 def config4_batch(num_trees: int = 4096, n_lo: float = 8.0, n_hi: float = 20.0) -> list[TreeSpec]:
     """Independent trees: n = floor(2^U(8,20)), d in {2,3,8,16}, half uniform
     half 8-cluster mixture, r in {4,16,64} by index mod r, cyclic, leaf <= 32.
@@ -210,7 +216,7 @@ def config4_batch(num_trees: int = 4096, n_lo: float = 8.0, n_hi: float = 20.0) 
         dist = "uniform" if rng.random() < 0.5 else "mixture8"
         r = int(rng.choice([4, 16, 64]))
         out.append(TreeSpec(f"batch{i}", n, d, dist, 1_000_000 + i, r, 0, 0, depth=0, leaf_size=32,
-                            max_levels=28))
+                            max_levels=leaf_mode_levels(n)))
     return out
 
 
@@ -228,7 +234,7 @@ def config5_stream(num_requests: int = 20000, rate: float = 100.0, n_lo: float =
         d = int(rng.choice([3, 16]))
         dist = "uniform" if rng.random() < 0.5 else "mixture8"
         specs.append(TreeSpec(f"req{i}", n, d, dist, 2_000_000 + i, 32, 0, 0, depth=0, leaf_size=64,
-                              max_levels=28))
+                              max_levels=leaf_mode_levels(n)))
     return t, specs
 
 

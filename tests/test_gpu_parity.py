@@ -132,7 +132,7 @@ def test_leaf_mode_config4_like_trees():
     specs = workloads.config4_batch(num_trees=24, n_lo=8.0, n_hi=16.0)
     for s in specs:
         pts = s.points()
-        check_against_oracle(pts, r=s.r, subset_mode=0, depth=0, leaf_size=32, max_levels=24)
+        check_against_oracle(pts, r=s.r, subset_mode=0, depth=0, leaf_size=32, max_levels=s.max_levels)
 
 
 # ------------------------------------------------------------- error paths
