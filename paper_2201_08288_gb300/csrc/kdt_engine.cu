@@ -195,6 +195,7 @@ Engine::Engine(const StepPlan& plan, uint8_t* base, cudaStream_t st) : plan_(pla
 
 kdt_status Engine::reset() {
   ENGINE_TRY(prepare_subtree_kernel());
+  ENGINE_TRY(prepare_scatter_kernel());
   const uint32_t mt = std::max<uint32_t>(plan_.needs.max_trees, 1);
   ENGINE_TRY(cudaMemsetAsync(words_, 0, W_COUNT * 4, st_));
   ENGINE_TRY(cudaMemsetAsync(slot_words_, 0, (size_t)S_COUNT * mt * 4, st_));
@@ -297,7 +298,7 @@ kdt_status Engine::tick() {
     s_.next_big = big_[cur_ ^ 1];
     const uint64_t nseg_bound = std::min<uint64_t>((uint64_t)big_count_ * KDT_MAX_SUBSETS, plan_.nseg_cap);
     launch_big_step(trees_, s_, plan_.max_tiles, (uint32_t)nseg_bound, plan_.bigseg_cap, root_dims_,
-                    plan_.needs.widest, plan_.needs.max_d, big_points_, st_);
+                    plan_.needs.widest, plan_.needs.max_d, big_points_, plan_.grid_sub, st_);
     ENGINE_TRY(cudaGetLastError());
     root_dims_ = false;
     uint32_t counts[4];

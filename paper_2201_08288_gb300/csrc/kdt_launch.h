@@ -56,7 +56,13 @@ inline int subtree_capacity(int d) {
 
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
                      uint32_t max_bigseg, bool need_root_dims, bool any_widest, int max_d, uint64_t points,
-                     cudaStream_t st);
+                     uint32_t sms, cudaStream_t st);
+
+// Dynamic shared memory of the staged scatter (two CTAs per SM).
+constexpr uint32_t kScatterSmemBytes = 100 * 1024;
+cudaError_t prepare_scatter_kernel();
+void launch_scatter(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t grid_cap,
+                    uint64_t points, cudaStream_t st);
 
 cudaError_t prepare_subtree_kernel();
 void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head, LCell* slices,

@@ -510,173 +510,6 @@ __global__ void k_part_scan(StepDev s) {
   if (threadIdx.x == 0) s.lcount[c] = run;
 }
 
-// Per tile: stable scatter of all columns, the permutation and the subset ids.
-// Point j of the tile (in position order) goes left to
-//   begin + (left points before the tile) + (left points before j in the tile)
-// or right to
-//   begin + L + (right points before the tile) + (right points before j).
-// A child that is terminal only receives the permutation, in out_perm. For
-// widest spread the tile also reduces each child's min and max per coordinate.
-__global__ void __launch_bounds__(kTileThreads) k_part_scatter(const TreeDev* trees, StepDev s) {
-  uint2 tl;
-  if (!tile_of(s, blockIdx.x, &tl)) return;
-  __shared__ uint32_t wcnt[kItems][kWarps];
-  __shared__ uint32_t wmm[kWarps][2][kMaxDims][2];
-  const Cell cell = s.cells[tl.x];
-  const TreeDev& t = trees[cell.tree];
-  const int level = cell.level;
-  const int64_t n = t.n;
-  const int d = t.d;
-  const float* X = src_cols(t, level) + cell.begin;
-  const uint32_t* P = src_perm(t, level);
-  const void* S = src_sid(t, level);
-  float* Xo = t.xbuf[level & 1];
-  uint32_t* Po = t.pbuf[level & 1];
-  void* So = t.sbuf[level & 1];
-  const bool explicit_sid = t.subset_mode == SUB_EXPLICIT;
-  const uint32_t dim = s.kdim[tl.x];
-  const uint32_t m = s.mkey[tl.x];
-  const uint32_t loff = s.tile_loff[blockIdx.x];
-  const uint32_t L = s.lcount[tl.x];
-  const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  // children that are terminal are never read again
-  const int child_stall = (cell.count == L) ? cell.stall + 1 : 0;
-  const bool term_left = is_terminal(t, L, level + 1, child_stall);
-  const bool term_right = is_terminal(t, cell.count - L, level + 1, child_stall);
-  const bool want_mm = t.key_rule == KEY_WIDEST && !(term_left && term_right);
-
-  // flags of the thread's points
-  float xk[kItems];
-#pragma unroll
-  for (int q = 0; q < kItems; ++q) {
-    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-    xk[q] = i < end ? X[(int64_t)dim * n + i] : 0.0f;
-  }
-  bool left[kItems];
-  unsigned bal[kItems];
-#pragma unroll
-  for (int q = 0; q < kItems; ++q) {
-    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-    left[q] = i < end && ord_key(xk[q]) <= m;
-    bal[q] = __ballot_sync(0xffffffffu, left[q]);
-    if (lane == 0) wcnt[q][warp] = __popc(bal[q]);
-  }
-  if (want_mm) {
-    for (int j = lane; j < 2 * d * 2; j += 32) {
-      const int side = j / (2 * d), l = (j / 2) % d, which = j & 1;
-      wmm[warp][side][l][which] = which ? 0u : 0xffffffffu;
-    }
-  }
-  __syncthreads();
-  // destinations, in position order: rounds q, then warps, then lanes
-  uint32_t dst[kItems];
-  {
-    uint32_t before = 0;
-#pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-      uint32_t in_round = 0, below_warp = 0;
-      for (int w = 0; w < kWarps; ++w) {
-        const uint32_t v = wcnt[q][w];
-        below_warp += (w < warp) ? v : 0u;
-        in_round += v;
-      }
-      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-      const uint32_t lrank = before + below_warp + __popc(bal[q] & lt_mask);
-      const uint32_t rrank = (i - tl.y) - lrank;  // right points of the tile before this one
-      dst[q] = left[q] ? cell.begin + loff + lrank : cell.begin + L + (tl.y - loff) + rrank;
-      before += in_round;
-    }
-  }
-  bool saw_nan = false;
-  // permutation
-  {
-    uint32_t pv[kItems];
-#pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-      const int64_t p = (int64_t)cell.begin + i;
-      pv[q] = (i < end) ? (P ? P[p] : (uint32_t)p) : 0u;
-    }
-#pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-      if (i >= end) continue;
-      if (left[q] ? term_left : term_right)
-        t.out_perm[dst[q]] = pv[q];
-      else
-        Po[dst[q]] = pv[q];
-    }
-  }
-  // coordinates
-  for (int l = 0; l < d; ++l) {
-    float x[kItems];
-#pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-      x[q] = (i < end) ? (l == (int)dim ? xk[q] : X[(int64_t)l * n + i]) : 0.0f;
-    }
-    uint32_t lmin = 0xffffffffu, lmax = 0u, rmin = 0xffffffffu, rmax = 0u;
-#pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-      if (i >= end) continue;
-      if (level == 0) saw_nan |= is_nan_bits(x[q]);
-      if (left[q] ? term_left : term_right) continue;
-      Xo[(int64_t)l * n + dst[q]] = x[q];
-      if (want_mm) {
-        const uint32_t k = ord_key(x[q]);
-        if (left[q]) {
-          lmin = min(lmin, k);
-          lmax = max(lmax, k);
-        } else {
-          rmin = min(rmin, k);
-          rmax = max(rmax, k);
-        }
-      }
-    }
-    if (want_mm) {
-      lmin = __reduce_min_sync(0xffffffffu, lmin);
-      lmax = __reduce_max_sync(0xffffffffu, lmax);
-      rmin = __reduce_min_sync(0xffffffffu, rmin);
-      rmax = __reduce_max_sync(0xffffffffu, rmax);
-      if (lane == 0) {
-        wmm[warp][0][l][0] = lmin;
-        wmm[warp][0][l][1] = lmax;
-        wmm[warp][1][l][0] = rmin;
-        wmm[warp][1][l][1] = rmax;
-      }
-    }
-  }
-  // subset ids
-  if (explicit_sid) {
-#pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-      if (i >= end || (left[q] ? term_left : term_right)) continue;
-      const int64_t p = (int64_t)cell.begin + i;
-      if (t.sid_bytes == 1)
-        ((uint8_t*)So)[dst[q]] = ((const uint8_t*)S)[p];
-      else
-        ((uint16_t*)So)[dst[q]] = ((const uint16_t*)S)[p];
-    }
-  }
-  if (saw_nan) set_status(t, ST_NAN_INPUT);
-  if (want_mm) {
-    __syncthreads();
-    for (int j = threadIdx.x; j < 2 * d * 2; j += blockDim.x) {
-      const int side = j / (2 * d), l = (j / 2) % d, which = j & 1;
-      uint32_t v = wmm[0][side][l][which];
-      for (int w = 1; w < kWarps; ++w) {
-        const uint32_t u = wmm[w][side][l][which];
-        v = which ? max(v, u) : min(v, u);
-      }
-      s.tile_mm[(((size_t)blockIdx.x * 2 + side) * kMaxDims + l) * 2 + which] = v;
-    }
-  }
-}
-
 // Grid (cell, side, coordinate): reduce the scatter's tile partials to each
 // child's min and max key per coordinate (widest spread only).
 __global__ void k_child_mm(const TreeDev* trees, StepDev s) {
@@ -767,7 +600,7 @@ __global__ void k_next(const TreeDev* trees, StepDev s) {
 
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
                      uint32_t max_bigseg, bool need_root_dims, bool any_widest, int max_d, uint64_t points,
-                     cudaStream_t st) {
+                     uint32_t sms, cudaStream_t st) {
   const uint32_t nc = s.ncells;
   if (nc == 0) return;
   { TraceScope ts(K_PREP, st); k_prep<<<1, 1024, 0, st>>>(trees, s); }
@@ -787,10 +620,7 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
   { TraceScope ts(K_COMBINE, st); k_combine<<<nc, 256, 0, st>>>(trees, s); }
   { TraceScope ts(K_PART_COUNT, st, points); k_part_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
   { TraceScope ts(K_PART_SCAN, st); k_part_scan<<<nc, 1024, 0, st>>>(s); }
-  {
-    TraceScope ts(K_PART_SCATTER, st, points);
-    k_part_scatter<<<max_tiles, kTileThreads, 0, st>>>(trees, s);
-  }
+  launch_scatter(trees, s, max_tiles, 2 * sms, points, st);
   if (any_widest) {
     TraceScope ts(K_CHILD_MM, st);
     k_child_mm<<<dim3(nc, 2, max_d), 256, 0, st>>>(trees, s);

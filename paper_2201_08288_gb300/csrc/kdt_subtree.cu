@@ -20,6 +20,7 @@
 
 #include "kdt_internal.cuh"
 #include "kdt_launch.h"
+#include "kdt_ptx.cuh"
 #include "kdt_trace.h"
 
 namespace kdt {
@@ -30,54 +31,6 @@ constexpr int T = kSubtreeThreads;
 constexpr int NW = kSubtreeWarps;
 constexpr uint16_t kNoCell = 0xffff;
 constexpr uint32_t kRankMax = 24;
-constexpr uint32_t kSpinLimit = 1u << 22;
-
-// ------------------------------------------------------------- PTX helpers
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(phase)
-      : "memory");
-  return done != 0;
-}
-
-// Bounded wait on an mbarrier phase: false if it did not complete in time.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
-    if (mbar_try_wait(bar, phase)) return true;
-  return false;
-}
-
-// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 // -------------------------------------------------------- shared layout
 
@@ -168,7 +121,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
                       slices + (size_t)blockIdx.x * 2 * slice_cells + slice_cells};
   if (tid == 0) {
     mbar_init(&s_bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
     s_fail = 0;
   }
   uint32_t phase = 0;
