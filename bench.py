@@ -54,24 +54,21 @@ def workload(name: str, rank: int):
 
 def bytes_per_point(kernel: str, d: int, sid_bytes: int, subset_mode: int) -> float:
     """Algorithmic bytes one launch moves per point it processes."""
-    sid_src = sid_bytes if subset_mode == 2 else 4  # explicit id column, else derived from perm
     return {
         "k_part_scatter": 2.0 * (4 * d + 4 + sid_bytes),   # read + write every column, perm, ids
         "k_subtree": 4.0 * d + 4 + sid_bytes + 4,           # stage everything once, write perm once
-        "k_group": 4.0 + sid_src + 4,                       # key + id in, key out
-        "k_seg_count": float(sid_src),
+        "k_ps_move": 2.0 * (4 * d + sid_bytes) + 4,         # columns and ids in and out, perm out
         "k_part_count": 4.0,
-        "k_select_small": 4.0,
+        "k_select_small": 4.0,                              # the key column, read in place
         "k_minmax": 4.0 * d,
     }.get(kernel, 0.0)
 
 
 def model_bytes_per_point_level(d: int, sid_bytes: int, subset_mode: int) -> float:
-    """Bytes each level must move per point (SoA ping-pong model): key read for
-    the select, the subset id source, read+write of all columns and the
+    """Bytes each level must move per point (SoA ping-pong model): the key
+    column read once for the selection, read+write of all columns and the
     permutation, read+write of an explicit id column."""
-    s_sel = sid_bytes if subset_mode == 2 else 4
-    return 4 + s_sel + 8 * (d + 1) + 2 * (sid_bytes if subset_mode == 2 else 0)
+    return 4 + 8 * (d + 1) + 2 * (sid_bytes if subset_mode == 2 else 0)
 
 
 class Clocks:

@@ -1,5 +1,7 @@
 // kdt_engine.cu -- the forest engine (see kdt_engine.h).
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "kdt_engine.h"
@@ -12,7 +14,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // Engine words.
-enum Word { W_NTILES = 0, W_BIGSEG, W_HEAD, W_NEXTBIG, W_SMALL, W_BIGPTS, W_SMALLPTS, W_COUNT };
+enum Word { W_NTILES = 0, W_BIGSEG, W_HEAD, W_NEXTBIG, W_SMALL, W_BIGPTS, W_SMALLPTS, W_OFFUSED, W_COUNT };
 // Per-slot words: [which][max_trees].
 enum SlotWord { S_TERM = 0, S_STATUS, S_LEVELS, S_LIVE, S_COUNT };
 
@@ -79,6 +81,9 @@ TreePlan plan_tree(const kdt_params& p) {
   t.L_cap = p.depth > 0 ? p.depth : p.max_levels;
   t.small_max = subtree_capacity(p.d);
   t.sid_bytes = p.subset_mode == KDT_SUBSET_EXPLICIT ? (p.subset_id16 ? 2 : 1) : 0;
+  const bool root_terminal = p.depth > 0 ? (n == 0) : (n <= (uint64_t)p.leaf_size);
+  t.presorted = !root_terminal && n > (uint64_t)t.small_max && p.subset_mode != KDT_SUBSET_CONTIGUOUS;
+  t.huge_cap = t.presorted ? n / (uint64_t)(kLeafBlockMax + 1) + 1 : 0;
   const uint64_t leaves = (uint64_t)1 << t.L_cap;
   t.maxB = std::min<uint64_t>(n / (uint64_t)(t.small_max + 1) + 1, leaves);
   t.cap_small = std::min<uint64_t>(n, leaves) + 1;
@@ -94,8 +99,11 @@ TreePlan plan_tree(const kdt_params& p) {
     t.pbuf[b] = take(n * 4);
     t.sbuf[b] = take(n * (size_t)t.sid_bytes);
   }
-  t.keys = take(n * 4);
   t.terms = take(t.term_cap * sizeof(TermRec));
+  t.root_off = take(((size_t)p.r + 1) * 4);
+  t.root_cur = take((size_t)p.r * 4);
+  t.huge = take(t.huge_cap * 4);
+  t.words = take(16);
   t.bytes = off;
   return t;
 }
@@ -119,6 +127,7 @@ StepPlan plan_step(const StepNeeds& needs) {
   s.cap_small = (uint32_t)std::min<uint64_t>(needs.cap_small, clamp);
   s.max_tiles = (uint32_t)std::min<uint64_t>(needs.points / kTile + needs.maxB + 1, clamp);
   s.nseg_cap = (uint32_t)std::min<uint64_t>(needs.nseg, clamp);
+  s.off_cap = (uint32_t)std::min<uint64_t>(needs.nseg + needs.maxB, clamp);
   s.bigseg_cap = (uint32_t)std::min<uint64_t>(needs.points / (kSelSmallMax + 1) + 1, clamp);
   const int sms = device_sms();
   s.grid_sub = (uint32_t)(sms > 0 ? sms : 148);
@@ -132,7 +141,7 @@ StepPlan plan_step(const StepNeeds& needs) {
   s.trees = take((size_t)mt * sizeof(TreeDev));
   s.words = take(W_COUNT * 4);
   s.slot_words = take((size_t)S_COUNT * mt * 4);
-  s.slots_list = take((size_t)mt * 4);
+  s.slots_list = take((size_t)mt * 2 * 4);
   s.big[0] = take((size_t)s.maxB * sizeof(Cell));
   s.big[1] = take((size_t)s.maxB * sizeof(Cell));
   s.small = take((size_t)s.cap_small * sizeof(Cell));
@@ -148,16 +157,22 @@ StepPlan plan_step(const StepNeeds& needs) {
   s.lcount = take((size_t)s.maxB * 4);
   s.seg_w = take((size_t)s.nseg_cap * 4);
   s.seg_beg = take((size_t)s.nseg_cap * 4);
-  s.seg_cur = take((size_t)s.nseg_cap * 4);
   s.seg_med = take((size_t)s.nseg_cap * 4);
   s.seg_cell = take((size_t)s.nseg_cap * 4);
   s.bigseg = take((size_t)s.bigseg_cap * 4);
   s.slices = take((size_t)s.grid_sub * 2 * needs.slice_cells * sizeof(LCell));
+  for (int b = 0; b < 2; ++b) {
+    s.off[b] = take((size_t)s.off_cap * 4);
+    s.obase[b] = take((size_t)s.maxB * 4);
+  }
+  s.crow = take((size_t)s.maxB * 2 * sizeof(uint2));
   s.bytes = off;
   return s;
 }
 
 Engine::Engine(const StepPlan& plan, uint8_t* base, cudaStream_t st) : plan_(plan), base_(base), st_(st) {
+  const char* dbg = std::getenv("KDT_DEBUG");
+  debug_ = dbg && *dbg && *dbg != '0';
   trees_ = (TreeDev*)(base + plan.trees);
   words_ = (uint32_t*)(base + plan.words);
   slot_words_ = (uint32_t*)(base + plan.slot_words);
@@ -177,7 +192,6 @@ Engine::Engine(const StepPlan& plan, uint8_t* base, cudaStream_t st) : plan_(pla
   s_.child_mm = (uint32_t*)(base + plan.child_mm);
   s_.seg_w = (uint32_t*)(base + plan.seg_w);
   s_.seg_beg = (uint32_t*)(base + plan.seg_beg);
-  s_.seg_cur = (uint32_t*)(base + plan.seg_cur);
   s_.seg_med = (uint32_t*)(base + plan.seg_med);
   s_.seg_cell = (uint32_t*)(base + plan.seg_cell);
   s_.bigseg = (uint32_t*)(base + plan.bigseg);
@@ -191,11 +205,23 @@ Engine::Engine(const StepPlan& plan, uint8_t* base, cudaStream_t st) : plan_(pla
   s_.next_big_cap = plan.maxB;
   s_.next_big_points = words_ + W_BIGPTS;
   s_.small_points = words_ + W_SMALLPTS;
+  for (int b = 0; b < 2; ++b) {
+    off_[b] = (uint32_t*)(base + plan.off[b]);
+    obase_[b] = (uint32_t*)(base + plan.obase[b]);
+  }
+  s_.off_used = words_ + W_OFFUSED;
+  s_.off_cap = plan.off_cap;
+  s_.bigseg_cap = plan.bigseg_cap;
+  s_.crow = (uint2*)(base + plan.crow);
+  const uint32_t mt = std::max<uint32_t>(plan.needs.max_trees, 1);
+  host_.assign(mt, TreeHost{});
+  presorted_.assign(mt, 0);
 }
 
 kdt_status Engine::reset() {
   ENGINE_TRY(prepare_subtree_kernel());
   ENGINE_TRY(prepare_scatter_kernel());
+  ENGINE_TRY(prepare_step_kernels());
   const uint32_t mt = std::max<uint32_t>(plan_.needs.max_trees, 1);
   ENGINE_TRY(cudaMemsetAsync(words_, 0, W_COUNT * 4, st_));
   ENGINE_TRY(cudaMemsetAsync(slot_words_, 0, (size_t)S_COUNT * mt * 4, st_));
@@ -224,6 +250,7 @@ kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p
   h.stall_limit = p.key_rule == KDT_KEY_CYCLIC ? p.d : 1;
   h.sid_bytes = tp.sid_bytes;
   h.small_max = tp.small_max;
+  h.presorted = tp.presorted ? 1 : 0;
   h.x_in = points;
   h.sid_in = p.subset_id16 ? (const void*)p.subset_id16 : (const void*)p.subset_id8;
   for (int b = 0; b < 2; ++b) {
@@ -231,7 +258,11 @@ kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p
     h.pbuf[b] = (uint32_t*)(tb + tp.pbuf[b]);
     h.sbuf[b] = (void*)(tb + tp.sbuf[b]);
   }
-  h.keys = (uint32_t*)(tb + tp.keys);
+  h.root_off = (uint32_t*)(tb + tp.root_off);
+  h.root_cur = (uint32_t*)(tb + tp.root_cur);
+  h.huge = (uint32_t*)(tb + tp.huge);
+  h.huge_count = (uint32_t*)(tb + tp.words);
+  h.huge_cap = (uint32_t)std::min<uint64_t>(tp.huge_cap, 0xffffffffull);
   h.out_perm = out_perm;
   h.out_vals = out_vals;
   h.out_dims = out_dims;
@@ -245,6 +276,11 @@ kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p
   ENGINE_TRY(cudaMemcpyAsync(trees_ + slot, &h, sizeof(h), cudaMemcpyHostToDevice, st_));
   for (int w = 0; w < S_COUNT; ++w)
     ENGINE_TRY(cudaMemsetAsync(slot_words_ + (size_t)w * mt + slot, 0, 4, st_));
+  ENGINE_TRY(cudaMemsetAsync(h.huge_count, 0, 4, st_));
+  presorted_[slot] = tp.presorted ? 1 : 0;
+  // after the build the tree's working buffers are free: the global leaf-sort
+  // passes use pbuf[0] as their second buffer and xbuf[0] for tile tables
+  host_[slot] = TreeHost{(uint64_t)p.n, out_perm, h.pbuf[0], (void*)h.xbuf[0], (size_t)p.d * p.n * 4};
 
   const uint64_t n = (uint64_t)p.n;
   const Cell root{0u, (uint32_t)n, 0u, (int32_t)slot, 0, 0, -1};
@@ -271,6 +307,7 @@ kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p
 
 kdt_status Engine::tick() {
   // new roots join the lists of this tick
+  const bool has_roots = !pending_big_.empty();
   if (!pending_big_.empty()) {
     if (big_count_ + pending_big_.size() > plan_.maxB) return KDT_ERR_CAPACITY;
     ENGINE_TRY(cudaMemcpyAsync(big_[cur_] + big_count_, pending_big_.data(), pending_big_.size() * sizeof(Cell),
@@ -293,17 +330,30 @@ kdt_status Engine::tick() {
   if (big_count_ > 0) {
     ENGINE_TRY(cudaMemsetAsync(words_ + W_NEXTBIG, 0, 4, st_));
     ENGINE_TRY(cudaMemsetAsync(words_ + W_BIGPTS, 0, 4, st_));
+    ENGINE_TRY(cudaMemsetAsync(words_ + W_OFFUSED, 0, 4, st_));
     s_.cells = big_[cur_];
     s_.ncells = big_count_;
     s_.next_big = big_[cur_ ^ 1];
+    s_.off_cur = off_[cur_];
+    s_.obase_cur = obase_[cur_];
+    s_.off_next = off_[cur_ ^ 1];
+    s_.obase_next = obase_[cur_ ^ 1];
     const uint64_t nseg_bound = std::min<uint64_t>((uint64_t)big_count_ * KDT_MAX_SUBSETS, plan_.nseg_cap);
-    launch_big_step(trees_, s_, plan_.max_tiles, (uint32_t)nseg_bound, plan_.bigseg_cap, root_dims_,
+    launch_big_step(trees_, s_, plan_.max_tiles, (uint32_t)nseg_bound, plan_.bigseg_cap, has_roots, root_dims_,
                     plan_.needs.widest, plan_.needs.max_d, big_points_, plan_.grid_sub, st_);
     ENGINE_TRY(cudaGetLastError());
     root_dims_ = false;
     uint32_t counts[4];
     ENGINE_TRY(cudaMemcpyAsync(counts, words_ + W_NEXTBIG, 16, cudaMemcpyDeviceToHost, st_));
     ENGINE_TRY(cudaStreamSynchronize(st_));
+    if (debug_) {  // KDT_DEBUG=1: per-tick counts and raw tree statuses on stderr
+      const uint32_t mt = std::max<uint32_t>(plan_.needs.max_trees, 1);
+      std::vector<int32_t> stv(mt);
+      ENGINE_TRY(cudaMemcpy(stv.data(), slot_words_ + (size_t)S_STATUS * mt, (size_t)mt * 4, cudaMemcpyDeviceToHost));
+      std::fprintf(stderr, "kdt tick: big %u -> %u, small %u\n", big_count_, counts[0], counts[1]);
+      for (uint32_t k = 0; k < mt; ++k)
+        if (stv[k]) std::fprintf(stderr, "kdt tick: slot %u status %d\n", k, stv[k]);
+    }
     big_count_ = std::min(counts[0], plan_.maxB);
     small_count_ = std::min(counts[1], plan_.cap_small);
     big_points_ = counts[2];
@@ -358,10 +408,39 @@ kdt_status Engine::finalize(const std::vector<uint32_t>& slots, std::vector<kdt_
       ok.push_back(s);
       max_rec = std::max(max_rec, tc[s]);
     }
+  std::vector<uint32_t> sorted;  // presorted trees: their leaves need the leaf sort
+  for (uint32_t s : ok)
+    if (presorted_[s]) sorted.push_back(s);
   if (!ok.empty()) {
     ENGINE_TRY(cudaMemcpyAsync(slots_list_, ok.data(), ok.size() * 4, cudaMemcpyHostToDevice, st_));
     launch_finalize_many(trees_, slots_list_, (uint32_t)ok.size(), max_rec, st_);
     ENGINE_TRY(cudaGetLastError());
+    if (!sorted.empty()) {
+      // the slot list is read by the finalize launch above: the sorted slots go after it
+      ENGINE_TRY(cudaMemcpyAsync(slots_list_ + ok.size(), sorted.data(), sorted.size() * 4,
+                                 cudaMemcpyHostToDevice, st_));
+      launch_leaf_sort(trees_, slots_list_ + ok.size(), (uint32_t)sorted.size(), max_rec, st_);
+      ENGINE_TRY(cudaGetLastError());
+    }
+    ENGINE_TRY(cudaStreamSynchronize(st_));
+  }
+  for (uint32_t s : sorted) {  // leaves too large for one CTA (shallow trees, cells that stop splitting)
+    TreeDev h;
+    uint32_t nh = 0;
+    ENGINE_TRY(cudaMemcpyAsync(&h, trees_ + s, sizeof(h), cudaMemcpyDeviceToHost, st_));
+    ENGINE_TRY(cudaStreamSynchronize(st_));
+    ENGINE_TRY(cudaMemcpyAsync(&nh, h.huge_count, 4, cudaMemcpyDeviceToHost, st_));
+    ENGINE_TRY(cudaStreamSynchronize(st_));
+    nh = std::min(nh, h.huge_cap);
+    if (nh == 0) continue;
+    std::vector<uint32_t> idx(nh);
+    std::vector<TermRec> all(std::min(tc[s], h.term_cap)), recs;
+    ENGINE_TRY(cudaMemcpyAsync(idx.data(), h.huge, (size_t)nh * 4, cudaMemcpyDeviceToHost, st_));
+    ENGINE_TRY(cudaMemcpyAsync(all.data(), h.terms, all.size() * sizeof(TermRec), cudaMemcpyDeviceToHost, st_));
+    ENGINE_TRY(cudaStreamSynchronize(st_));
+    for (uint32_t k : idx)
+      if (k < all.size()) recs.push_back(all[k]);
+    ENGINE_TRY(leaf_sort_huge(host_[s], recs, st_));
     ENGINE_TRY(cudaStreamSynchronize(st_));
   }
   for (size_t i = 0; i < slots.size(); ++i) {

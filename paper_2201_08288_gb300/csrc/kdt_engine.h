@@ -26,11 +26,14 @@ struct TreePlan {
   int L_cap = 0;
   int small_max = 0;
   int sid_bytes = 0;
+  bool presorted = false;  // big root and subsets not already in index order
   uint64_t n = 0;
   uint64_t term_cap = 0;
+  uint64_t huge_cap = 0;  // terminal cells larger than one CTA's leaf sort
   uint64_t maxB = 0;      // big cells at one level
   uint64_t cap_small = 0; // small cells over the whole build
-  size_t xbuf[2] = {0, 0}, pbuf[2] = {0, 0}, sbuf[2] = {0, 0}, keys = 0, terms = 0;
+  size_t xbuf[2] = {0, 0}, pbuf[2] = {0, 0}, sbuf[2] = {0, 0}, terms = 0, root_off = 0, root_cur = 0,
+         huge = 0, words = 0;
   size_t bytes = 0;
 };
 TreePlan plan_tree(const kdt_params& p);
@@ -47,11 +50,11 @@ struct StepNeeds {
 
 struct StepPlan {
   StepNeeds needs;
-  uint32_t maxB = 0, cap_small = 0, max_tiles = 0, nseg_cap = 0, bigseg_cap = 0, grid_sub = 0;
+  uint32_t maxB = 0, cap_small = 0, max_tiles = 0, nseg_cap = 0, bigseg_cap = 0, grid_sub = 0, off_cap = 0;
   size_t trees = 0, words = 0, slot_words = 0, slots_list = 0, big[2] = {0, 0}, small = 0, tile_base = 0,
          seg_base = 0, tiles = 0, tile_left = 0, tile_loff = 0, tile_mm = 0, child_mm = 0, kdim = 0,
-         mkey = 0, lcount = 0, seg_w = 0, seg_beg = 0, seg_cur = 0, seg_med = 0, seg_cell = 0,
-         bigseg = 0, slices = 0;
+         mkey = 0, lcount = 0, seg_w = 0, seg_beg = 0, seg_med = 0, seg_cell = 0, bigseg = 0, slices = 0,
+         off[2] = {0, 0}, obase[2] = {0, 0}, crow = 0;
   size_t bytes = 0;
 };
 StepPlan plan_step(const StepNeeds& needs);
@@ -86,6 +89,8 @@ class Engine {
   uint32_t* slot_words_ = nullptr;  // device [4][max_trees]: term_count, status, levels, live
   uint32_t* slots_list_ = nullptr;  // device [max_trees]
   Cell* big_[2] = {nullptr, nullptr};
+  uint32_t* off_[2] = {nullptr, nullptr};
+  uint32_t* obase_[2] = {nullptr, nullptr};
   Cell* small_ = nullptr;
   LCell* slices_ = nullptr;
   StepDev s_{};
@@ -93,7 +98,10 @@ class Engine {
   uint32_t big_count_ = 0, small_count_ = 0;
   uint64_t big_points_ = 0, small_points_ = 0;
   bool root_dims_ = false;
+  bool debug_ = false;
   std::vector<Cell> pending_big_, pending_small_;
+  std::vector<TreeHost> host_;       // per slot: leaf-sort view of a presorted tree
+  std::vector<uint8_t> presorted_;   // per slot
 };
 
 }  // namespace kdt

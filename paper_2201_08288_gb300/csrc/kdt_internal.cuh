@@ -6,6 +6,16 @@
 // combined from per-subset medians (the subsets of Sec. 3.2 / App. C.2); the
 // per-subset statistic is the lower median and the combination is the
 // count-weighted lower median of those medians.
+//
+// Layout invariant of the multi-CTA pipeline: inside every cell the points are
+// ordered by subset, so each (cell, subset) segment is one contiguous range.
+// The root is reordered once by subset (a counting pass; closed form for
+// subsets by index mod r; nothing to do for contiguous subsets), and the
+// stable two-way partition of every level keeps the order. The medians, the
+// splits and the cell sizes do not depend on the order of points inside a
+// cell; the one output that does, the order of the permutation inside each
+// leaf, is ascending original index in the sequential definition (stable
+// partitions of the identity), and a final per-leaf sort restores it.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -34,6 +44,7 @@ enum : int32_t {
   ST_CAPACITY = 5,
   ST_TIMEOUT = 6,
   ST_LEVEL_CAP = 7,
+  ST_INTERNAL = 9,  // an internal table was inconsistent (reported as a CUDA error)
 };
 
 enum : int32_t { KEY_CYCLIC = 0, KEY_WIDEST = 1 };
@@ -43,8 +54,9 @@ enum : int32_t { SUB_MOD = 0, SUB_CONTIG = 1, SUB_EXPLICIT = 2 };
 
 // Everything a kernel needs to know about one tree. Level l reads its points
 // from src(l) and the multi-CTA partition writes them to dst(l):
-//   src(0) = caller input (perm = identity), src(l>0) = buf[(l-1)&1],
-//   dst(l) = buf[l&1].
+//   src(0) = the root reordered by subset in buf[1] (presorted trees), else
+//            the caller's input (perm = identity);
+//   src(l>0) = buf[(l-1)&1], dst(l) = buf[l&1].
 struct TreeDev {
   int64_t n;
   int32_t d, r, subset_mode, key_rule;
@@ -54,13 +66,18 @@ struct TreeDev {
   int32_t stall_limit; // d (cyclic) or 1 (widest)
   int32_t sid_bytes;   // explicit mode: 1 or 2
   int32_t small_max;   // cells up to this size finish in the subtree kernel
-  int32_t pad0;
+  int32_t presorted;   // root reordered by subset into buf[1]; leaves sorted at the end
   const float* x_in;
   const void* sid_in;
   float* xbuf[2];
   uint32_t* pbuf[2];
   void* sbuf[2];
-  uint32_t* keys;        // [n] per-level scratch (keys grouped by (cell, subset))
+  uint32_t* root_off;    // [r+1] subset offsets of the root (level 0)
+  uint32_t* root_cur;    // [r] subset counts, then fill cursors of the presort
+  uint32_t* huge;        // [huge_cap] terminal records too large for one CTA's leaf sort
+  uint32_t* huge_count;  // device word
+  uint32_t huge_cap;
+  uint32_t pad2;
   uint32_t* out_perm;
   float* out_vals;
   int8_t* out_dims;
@@ -112,11 +129,10 @@ struct StepDev {
                           // root per tile of the cell itself, after the scatter per child side
   uint32_t* child_mm;     // [ncells][2][kMaxDims][2] per-child min/max keys (widest)
   uint32_t* seg_w;        // [nseg] points per (cell, subset)
-  uint32_t* seg_beg;      // [nseg] absolute scratch position
-  uint32_t* seg_cur;      // [nseg] fill cursor
+  uint32_t* seg_beg;      // [nseg] position of the segment in its tree's current order
   uint32_t* seg_med;      // [nseg] lower median key
   uint32_t* seg_cell;     // [nseg] owning cell
-  uint32_t* bigseg;       // [cap] segments larger than kSelSmallMax
+  uint32_t* bigseg;       // [bigseg_cap] segments larger than kSelSmallMax
   uint32_t* bigseg_count; // device word
   uint32_t* tile_left;    // [ntiles]
   uint32_t* tile_loff;    // [ntiles]
@@ -128,7 +144,20 @@ struct StepDev {
   uint32_t small_cap;
   uint32_t* next_big_points;  // points in next_big (for bandwidth accounting)
   uint32_t* small_points;     // points appended to small
+  // subset offsets (relative to the cell's begin, r+1 per cell) of this
+  // step's cells: rows of off_cur at obase_cur[c]; level-0 cells use their
+  // tree's root_off. The scatter fills the rows of the big children.
+  const uint32_t* off_cur;
+  const uint32_t* obase_cur;  // [ncells]
+  uint32_t* off_next;
+  uint32_t* obase_next;       // [next_big_cap]
+  uint32_t* off_used;         // device word: words of off_next handed out
+  uint32_t off_cap;
+  uint32_t bigseg_cap;
+  uint2* crow;                // [ncells][2] (slot, row of off_next) of each big child, else kNoRow
 };
+
+constexpr uint32_t kNoRow = 0xffffffffu;
 
 // ------------------------------------------------------------- key transform
 
@@ -151,13 +180,13 @@ __device__ __forceinline__ bool is_nan_bits(float x) {
 // -------------------------------------------------------------- tree views
 
 __device__ __forceinline__ const float* src_cols(const TreeDev& t, int level) {
-  return level == 0 ? t.x_in : t.xbuf[(level - 1) & 1];
+  return (level == 0 && !t.presorted) ? t.x_in : t.xbuf[(level - 1) & 1];
 }
 __device__ __forceinline__ const uint32_t* src_perm(const TreeDev& t, int level) {
-  return level == 0 ? nullptr : t.pbuf[(level - 1) & 1];
+  return (level == 0 && !t.presorted) ? nullptr : t.pbuf[(level - 1) & 1];
 }
 __device__ __forceinline__ const void* src_sid(const TreeDev& t, int level) {
-  return level == 0 ? t.sid_in : t.sbuf[(level - 1) & 1];
+  return (level == 0 && !t.presorted) ? t.sid_in : t.sbuf[(level - 1) & 1];
 }
 
 __device__ __forceinline__ void set_status(const TreeDev& t, int32_t code) {
@@ -179,6 +208,24 @@ __device__ __forceinline__ uint32_t subset_of(const TreeDev& t, const void* sidc
     return 0;
   }
   return s;
+}
+
+// Subset of a point from its original index (modes that define it so).
+__device__ __forceinline__ uint32_t subset_from_orig(const TreeDev& t, uint32_t orig) {
+  if (t.subset_mode == SUB_MOD) return orig % (uint32_t)t.r;
+  return (uint32_t)(((uint64_t)orig * (uint64_t)t.r) / (uint64_t)t.n);
+}
+
+// Subset of the point at position pos of the order level `level` reads
+// (explicit ids there are already checked and below r).
+__device__ __forceinline__ uint32_t subset_at(const TreeDev& t, int level, int64_t pos) {
+  if (t.subset_mode == SUB_EXPLICIT) {
+    const void* S = src_sid(t, level);
+    const uint32_t v = t.sid_bytes == 1 ? (uint32_t)((const uint8_t*)S)[pos] : (uint32_t)((const uint16_t*)S)[pos];
+    return min(v, (uint32_t)t.r - 1u);
+  }
+  const uint32_t* P = src_perm(t, level);
+  return subset_from_orig(t, P ? P[pos] : (uint32_t)pos);
 }
 
 // Terminal test for a cell about to be processed at `level` (reading R8 in

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "kdt_internal.cuh"
@@ -54,9 +55,10 @@ inline int subtree_capacity(int d) {
   return lo & ~31;
 }
 
+cudaError_t prepare_step_kernels();
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
-                     uint32_t max_bigseg, bool need_root_dims, bool any_widest, int max_d, uint64_t points,
-                     uint32_t sms, cudaStream_t st);
+                     uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d,
+                     uint64_t points, uint32_t sms, cudaStream_t st);
 
 // Dynamic shared memory of the staged scatter (two CTAs per SM).
 constexpr uint32_t kScatterSmemBytes = 100 * 1024;
@@ -69,6 +71,26 @@ void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint
                     uint32_t slice_cells, uint32_t grid, uint64_t points, cudaStream_t st);
 
 void launch_iota(uint32_t* out, uint32_t n, cudaStream_t st);
+
+// Leaf sort (kdt_leafsort.cu): terminal cells up to kLeafWarpMax points are
+// sorted by one warp, up to kLeafBlockMax by one CTA; larger ones are listed
+// in the tree's `huge` table and sorted by leaf_sort_huge.
+constexpr int kLeafWarpMax = 256;
+constexpr int kLeafBlockMax = 4096;
+void launch_leaf_sort(const TreeDev* trees, const uint32_t* slots, uint32_t nslots, uint32_t max_records,
+                      cudaStream_t st);
+// Host view of a finished tree for the global leaf-sort passes: the
+// permutation, a ping-pong buffer of n words and scratch for tile tables
+// (the tree's working buffers, free once its build is done).
+struct TreeHost {
+  uint64_t n;
+  uint32_t* out_perm;
+  uint32_t* keys;
+  void* scratch;
+  size_t scratch_bytes;
+};
+size_t leaf_huge_tiles_cap(uint64_t n);
+cudaError_t leaf_sort_huge(const TreeHost& th, const std::vector<TermRec>& recs, cudaStream_t st);
 
 }  // namespace kdt
 

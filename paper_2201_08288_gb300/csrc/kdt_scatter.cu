@@ -17,7 +17,10 @@
 //     shared memory to its destination, and release the buffer.
 // A child that is terminal receives only its permutation, in out_perm. For
 // widest spread the consumers also reduce each child's min and max key per
-// coordinate.
+// coordinate. Points of a cell arrive in subset order (contiguous segments),
+// and a stable partition keeps that order in both children; where the subset
+// changes, the consumers write where each big child's segments start (its
+// left or right rank there), which is the children's subset offset table.
 #include <algorithm>
 
 #include "kdt_internal.cuh"
@@ -49,6 +52,8 @@ struct SubMeta {
   TreeDev t;
   Cell cell;
   uint32_t tile, sub, mcnt, T, dim, mkey, L, loff, tile_start;
+  uint32_t row[2];            // rows of the children's subset offsets (kNoRow: not a big child)
+  uint32_t prev_sub;          // subset of the point before the sub-tile (~0u at the cell's start)
   uint32_t ph[kMaxDims + 1];  // alignment phase of each staged column
 };
 
@@ -57,6 +62,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
   __shared__ __align__(8) uint64_t full[2], empty[2];
   __shared__ SubMeta meta[2];
   __shared__ uint32_t wcnt[kMaxItems][kCW];
+  __shared__ uint32_t sedge[kMaxItems][kCW];  // subset of each warp's last point per round
   __shared__ uint32_t wmm[kCW][2][kMaxDims][2];
   __shared__ uint32_t s_fail;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -92,6 +98,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       const float* X = src_cols(tg, c.level);
       const uint32_t* P = src_perm(tg, c.level);
       const uint32_t dim = s.kdim[tl.x], mkey = s.mkey[tl.x], L = s.lcount[tl.x], loff = s.tile_loff[tile];
+      const uint2 cr0 = s.crow[2 * tl.x], cr1 = s.crow[2 * tl.x + 1];
       for (uint32_t sub = tl.y; sub < tend; sub += T, ++k) {
         const int b = k & 1;
         if (k >= 2) {
@@ -119,6 +126,11 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           m.L = L;
           m.loff = loff;
           m.tile_start = tl.y;
+          m.row[0] = cr0.x == kNoRow ? kNoRow : cr0.y;
+          m.row[1] = cr1.x == kNoRow ? kNoRow : cr1.y;
+          m.prev_sub = (sub > 0u && (cr0.x != kNoRow || cr1.x != kNoRow))
+                           ? subset_at(tg, c.level, (int64_t)g0 - 1)
+                           : 0xffffffffu;
         }
         uint32_t* A = sm + (size_t)b * (kBufBytes / 4);
         uint32_t total = 0;
@@ -212,19 +224,27 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       }
       const uint32_t* A = sm + (size_t)b * (kBufBytes / 4);
 
-      // ---- flags and ranks (position order)
+      // ---- flags and ranks (position order); subsets where offsets are kept
       bool left[kMaxItems];
       unsigned bal[kMaxItems];
+      uint32_t sv[kMaxItems];
+      const bool want_off = m.row[0] != kNoRow || m.row[1] != kNoRow;
       const uint32_t* keycol = A + (size_t)m.dim * stride + m.ph[m.dim];
+      const uint32_t* pa = A + (size_t)d * stride + m.ph[d];
 #pragma unroll
       for (int q = 0; q < kMaxItems; ++q) {
         const uint32_t i = tid + q * kCT;
         left[q] = i < mcnt && ord_key(__uint_as_float(keycol[i])) <= m.mkey;
         bal[q] = __ballot_sync(0xffffffffu, left[q]);
         if (lane == 0) wcnt[q][warp] = __popc(bal[q]);
+        sv[q] = 0;
+        if (want_off) {
+          if (i < mcnt) sv[q] = explicit_sid ? min(sidv[q], (uint32_t)t.r - 1u) : subset_from_orig(t, pa[i]);
+          if (lane == 31) sedge[q][warp] = sv[q];
+        }
       }
       named_sync(kConsumerBar, kCT);
-      uint32_t dst[kMaxItems];
+      uint32_t dst[kMaxItems], lrk[kMaxItems];
       uint32_t nL = 0;
 #pragma unroll
       for (int q = 0; q < kMaxItems; ++q) {
@@ -238,6 +258,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         const uint32_t i = tid + q * kCT;
         const uint32_t lr = nL + below + __popc(bal[q] & lt_mask);
         dst[q] = left[q] ? lnext + lr : rnext + (i - lr);
+        lrk[q] = lnext - cell.begin + lr;  // points of the cell before this one that go left
         nL += round;
       }
 
@@ -301,6 +322,30 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
             ((uint8_t*)So)[dst[q]] = (uint8_t)sidv[q];
           else
             ((uint16_t*)So)[dst[q]] = (uint16_t)sidv[q];
+        }
+      }
+      // ---- subset offsets of the big children, at the segment starts
+      // (each row holds r + 1 words below off_cap, checked when it was handed out)
+      if (want_off) {
+        const uint32_t r = (uint32_t)t.r;
+#pragma unroll
+        for (int q = 0; q < kMaxItems; ++q) {
+          const uint32_t i = tid + q * kCT;
+          const uint32_t p = m.sub + i;  // position in the cell
+          int32_t sp = __shfl_up_sync(0xffffffffu, (int32_t)sv[q], 1);
+          if (lane == 0)
+            sp = (int32_t)(warp > 0 ? sedge[q][warp - 1] : (q > 0 ? sedge[q - 1][kCW - 1] : m.prev_sub));
+          if (i >= mcnt) continue;
+          if ((int32_t)sv[q] != sp)
+            for (uint32_t u = (uint32_t)(sp + 1); u <= sv[q]; ++u) {
+              if (m.row[0] != kNoRow) s.off_next[m.row[0] + u] = lrk[q];
+              if (m.row[1] != kNoRow) s.off_next[m.row[1] + u] = p - lrk[q];
+            }
+          if (p + 1 == cell.count)
+            for (uint32_t u = sv[q] + 1; u <= r; ++u) {
+              if (m.row[0] != kNoRow) s.off_next[m.row[0] + u] = L;
+              if (m.row[1] != kNoRow) s.off_next[m.row[1] + u] = cell.count - L;
+            }
         }
       }
       lnext += nL;

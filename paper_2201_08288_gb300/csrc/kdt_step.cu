@@ -3,18 +3,23 @@
 //
 // For every big cell c of the step (paper, Sec. 2: a level splits each of its
 // cells along the key coordinate t at a median):
+//   0. (roots only) the points are reordered by subset (counting pass, or
+//      closed form for subsets by index mod r), so that every (cell, subset)
+//      segment is contiguous from then on;
 //   1. key coordinate: cyclic (Sec. 1) or widest range (Sec. 1, Friedman
 //      rule; computed for the root here, for every other cell by the parent's
 //      scatter, which reduces each child's per-coordinate min and max while it
 //      moves the columns);
-//   2. per (cell, subset) segment: count, then the keys grouped by segment
-//      into a scratch array (the subsets of Sec. 3.2 / App. C.2);
-//   3. per segment: the exact lower median (8-bit MSD radix select);
+//   2. per (cell, subset) segment (the subsets of Sec. 3.2 / App. C.2): its
+//      position range, from the cell's subset offsets;
+//   3. per segment: the exact lower median (8-bit MSD radix select) read in
+//      place from the key column;
 //   4. per cell: the count-weighted lower median of the segment medians;
-//   5. stable partition of all d columns, the permutation and the subset ids
-//      around the split (key <= split to the left) from per-tile counts and a
-//      per-cell scan of them;
-//   6. children: terminal / small (subtree kernel) / big (next step).
+//   5. children sizes from per-tile counts and a per-cell scan of them; the
+//      children are classified (terminal / small / big) before the move;
+//   6. stable partition of all d columns, the permutation and the subset ids
+//      around the split (key <= split to the left); the scatter also writes
+//      the big children's subset offsets.
 // Work is split into tiles of kTile points of one cell; a thread owns kItems
 // points of a tile (strided by the block size, so every load is coalesced)
 // and issues all of its loads before it uses any of them.
@@ -22,6 +27,7 @@
 
 #include "kdt_internal.cuh"
 #include "kdt_launch.h"
+#include "kdt_ptx.cuh"
 #include "kdt_trace.h"
 
 namespace kdt {
@@ -30,47 +36,16 @@ namespace {
 
 constexpr int kItems = kTile / kTileThreads;
 constexpr int kWarps = kTileThreads / 32;
+constexpr int kPsGroup = 4;                       // tiles per block of the root presort
+constexpr int kPsPoints = kPsGroup * kTile;
+constexpr int kPsThreads = 1024;
+constexpr int kPsItems = kPsPoints / kPsThreads;
+constexpr size_t kPsSmemBytes = (size_t)kPsPoints * 6;  // one word and one u16 subset per point
 
 __device__ __forceinline__ bool tile_of(const StepDev& s, uint32_t tile, uint2* out) {
   if (tile >= *s.ntiles_total) return false;
   *out = s.tiles[tile];
   return true;
-}
-
-// Subset ids of a thread's points: raw loads first, then the mapping.
-__device__ __forceinline__ void load_subsets(const TreeDev& t, const void* S, const uint32_t* P,
-                                             uint32_t begin, uint32_t i0, uint32_t end,
-                                             uint32_t (&sub)[kItems]) {
-  uint32_t raw[kItems];
-#pragma unroll
-  for (int q = 0; q < kItems; ++q) {
-    const uint32_t i = i0 + threadIdx.x + q * kTileThreads;
-    const int64_t p = (int64_t)begin + i;
-    raw[q] = 0;
-    if (i < end) {
-      if (t.subset_mode == SUB_EXPLICIT)
-        raw[q] = t.sid_bytes == 1 ? (uint32_t)((const uint8_t*)S)[p] : (uint32_t)((const uint16_t*)S)[p];
-      else
-        raw[q] = P ? P[p] : (uint32_t)p;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < kItems; ++q) {
-    const uint32_t i = i0 + threadIdx.x + q * kTileThreads;
-    sub[q] = 0xffffffffu;
-    if (i < end) {
-      if (t.subset_mode == SUB_MOD) {
-        sub[q] = raw[q] % (uint32_t)t.r;
-      } else if (t.subset_mode == SUB_CONTIG) {
-        sub[q] = (uint32_t)(((uint64_t)raw[q] * (uint64_t)t.r) / (uint64_t)t.n);
-      } else if (raw[q] < (uint32_t)t.r) {
-        sub[q] = raw[q];
-      } else {
-        set_status(t, ST_INVALID_ARG);
-        sub[q] = 0;
-      }
-    }
-  }
 }
 
 // ---------------------------------------------------------------- prep
@@ -111,14 +86,179 @@ __global__ void k_prep(const TreeDev* trees, StepDev s) {
   }
 }
 
-// One CTA per cell: tile list entries and zeroed segment counts.
-__global__ void k_tiles(StepDev s) {
+// One CTA per cell: tile list entries; zeroed subset counts of a presorted root.
+__global__ void k_tiles(const TreeDev* trees, StepDev s) {
   const uint32_t c = blockIdx.x;
   const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
   for (uint32_t j = tb + threadIdx.x; j < te; j += blockDim.x)
     s.tiles[j] = make_uint2(c, (j - tb) * (uint32_t)kTile);
-  const uint32_t sb = s.seg_base[c], se = s.seg_base[c + 1];
-  for (uint32_t g = sb + threadIdx.x; g < se; g += blockDim.x) s.seg_w[g] = 0;
+  const Cell cell = s.cells[c];
+  if (cell.level == 0) {
+    const TreeDev& t = trees[cell.tree];
+    if (t.presorted)
+      for (int j = threadIdx.x; j < t.r; j += blockDim.x) t.root_cur[j] = 0;
+  }
+}
+
+// ------------------------------------------------------ root presort
+
+__device__ __forceinline__ bool presort_tile(const TreeDev* trees, const StepDev& s, uint32_t tile, uint2* tl,
+                                             Cell* cell) {
+  if (!tile_of(s, tile, tl)) return false;
+  *cell = s.cells[tl->x];
+  return cell->level == 0 && trees[cell->tree].presorted;
+}
+
+// Per tile of a presorted root with explicit subset ids: points per subset.
+__global__ void __launch_bounds__(kTileThreads) k_ps_count(const TreeDev* trees, StepDev s) {
+  uint2 tl;
+  Cell cell;
+  if (!presort_tile(trees, s, blockIdx.x, &tl, &cell)) return;
+  const TreeDev& t = trees[cell.tree];
+  if (t.subset_mode != SUB_EXPLICIT) return;
+  __shared__ uint32_t hist[kMaxSubsets];
+  for (int j = threadIdx.x; j < t.r; j += blockDim.x) hist[j] = 0;
+  __syncthreads();
+  const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
+  uint32_t sub[kItems];
+#pragma unroll
+  for (int q = 0; q < kItems; ++q) {
+    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+    sub[q] = i < end ? subset_of(t, t.sid_in, 0u, (int64_t)i) : 0xffffffffu;
+  }
+#pragma unroll
+  for (int q = 0; q < kItems; ++q)
+    if (sub[q] != 0xffffffffu) atomic_add_shared(&hist[sub[q]], 1u);
+  __syncthreads();
+  for (int j = threadIdx.x; j < t.r; j += blockDim.x)
+    if (hist[j]) atomicAdd(&t.root_cur[j], hist[j]);
+}
+
+// One CTA per root cell: its subset offsets (r + 1 entries). Explicit ids:
+// exclusive scan of the counts (which also become the fill cursors); subsets
+// by index mod r: r_j = floor(n/r) + [j < n mod r] points each; contiguous
+// subsets (already in order): subset j starts at ceil(j n / r).
+__global__ void k_ps_offsets(const TreeDev* trees, StepDev s) {
+  __shared__ uint32_t tmp[33];
+  const Cell cell = s.cells[blockIdx.x];
+  if (cell.level != 0) return;
+  const TreeDev& t = trees[cell.tree];
+  const uint32_t r = (uint32_t)t.r, n = cell.count;
+  if (t.subset_mode == SUB_EXPLICIT) {
+    uint32_t run = 0;
+    for (uint32_t j0 = 0; j0 < r; j0 += blockDim.x) {
+      const uint32_t j = j0 + threadIdx.x;
+      const uint32_t v = j < r ? t.root_cur[j] : 0u;
+      uint32_t tot;
+      const uint32_t ex = block_excl_scan(v, tmp, &tot);
+      if (j < r) {
+        t.root_off[j] = run + ex;
+        t.root_cur[j] = run + ex;
+      }
+      run += tot;
+    }
+    if (threadIdx.x == 0) {
+      t.root_off[r] = run;
+      if (run != n) set_status(t, ST_INTERNAL);
+    }
+  } else if (t.subset_mode == SUB_MOD) {
+    const uint32_t q = n / r, rem = n % r;
+    for (uint32_t j = threadIdx.x; j <= r; j += blockDim.x) t.root_off[j] = j * q + min(j, rem);
+  } else {
+    for (uint32_t j = threadIdx.x; j <= r; j += blockDim.x)
+      t.root_off[j] = (uint32_t)(((uint64_t)j * n + r - 1) / r);
+  }
+}
+
+// Per group of kPsGroup consecutive tiles of a presorted root (kPsPoints
+// points): every point gets a rank inside its subset within the group
+// (shared-memory counter; order inside a subset is immaterial, see
+// kdt_internal.cuh), each subset of the group reserves a run of its place in
+// subset order (explicit ids: from the fill cursors; index mod r: closed
+// form), and every column passes through shared memory in subset order so
+// that the stores are contiguous runs of about kPsPoints / r points.
+__global__ void __launch_bounds__(kPsThreads) k_ps_move(const TreeDev* trees, StepDev s) {
+  uint2 tl;
+  Cell cell;
+  if (!presort_tile(trees, s, blockIdx.x, &tl, &cell)) return;
+  if ((tl.y / (uint32_t)kTile) % (uint32_t)kPsGroup != 0u) return;  // the group's first tile runs it
+  const TreeDev& t = trees[cell.tree];
+  extern __shared__ __align__(16) uint32_t ps_buf[];  // kPsPoints words, then kPsPoints u16 subsets
+  uint16_t* lsub = (uint16_t*)(ps_buf + kPsPoints);
+  __shared__ uint32_t loff[kMaxSubsets];   // counts, then local offsets
+  __shared__ uint32_t gbase[kMaxSubsets];  // global start of each subset's run
+  __shared__ uint32_t tmp[33];
+  const uint32_t r = (uint32_t)t.r, i0 = tl.y, end = min(i0 + (uint32_t)kPsPoints, cell.count);
+  const uint32_t m = end - i0;
+  const bool expl = t.subset_mode == SUB_EXPLICIT;
+  for (uint32_t j = threadIdx.x; j < r; j += kPsThreads) loff[j] = 0;
+  __syncthreads();
+  uint32_t sub[kPsItems], lp[kPsItems];
+#pragma unroll
+  for (int q = 0; q < kPsItems; ++q) {
+    const uint32_t i = i0 + threadIdx.x + q * kPsThreads;
+    sub[q] = i < end ? (expl ? subset_of(t, t.sid_in, 0u, (int64_t)i) : i % r) : 0xffffffffu;
+  }
+#pragma unroll
+  for (int q = 0; q < kPsItems; ++q) lp[q] = sub[q] != 0xffffffffu ? atomic_add_shared(&loff[sub[q]], 1u) : 0u;
+  __syncthreads();
+  uint32_t run = 0;
+  for (uint32_t j0 = 0; j0 < r; j0 += kPsThreads) {
+    const uint32_t j = j0 + threadIdx.x;
+    const uint32_t c = j < r ? loff[j] : 0u;
+    if (j < r) {
+      if (expl)
+        gbase[j] = c ? atomicAdd(&t.root_cur[j], c) : 0u;
+      else  // indices below i0 in subset j: floor(i0 / r) + [j < i0 mod r]
+        gbase[j] = t.root_off[j] + i0 / r + (j < i0 % r ? 1u : 0u);
+    }
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(c, tmp, &tot);
+    if (j < r) loff[j] = run + ex;
+    run += tot;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kPsItems; ++q)
+    if (sub[q] != 0xffffffffu) {
+      lp[q] += loff[sub[q]];
+      lsub[lp[q]] = (uint16_t)sub[q];
+    }
+  __syncthreads();
+  // place a value per point in subset order, then store the runs
+  auto pass = [&](auto value_of, auto store) {
+#pragma unroll
+    for (int q = 0; q < kPsItems; ++q)
+      if (sub[q] != 0xffffffffu) ps_buf[lp[q]] = value_of(q);
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < m; j += kPsThreads) {
+      const uint32_t sj = lsub[j];
+      const uint32_t dst = gbase[sj] + (j - loff[sj]);
+      if (dst < cell.count) store(dst, ps_buf[j]); else set_status(t, ST_INTERNAL);
+    }
+    __syncthreads();
+  };
+  const int64_t n = t.n;
+  for (int l = 0; l < t.d; ++l) {
+    const uint32_t* X = (const uint32_t*)(t.x_in + (int64_t)l * n);
+    uint32_t x[kPsItems];
+#pragma unroll
+    for (int q = 0; q < kPsItems; ++q) {
+      const uint32_t i = i0 + threadIdx.x + q * kPsThreads;
+      x[q] = i < end ? X[i] : 0u;
+    }
+    uint32_t* out = (uint32_t*)(t.xbuf[1] + (int64_t)l * n);
+    pass([&](int q) { return x[q]; }, [&](uint32_t dst, uint32_t v) { out[dst] = v; });
+  }
+  pass([&](int q) { return i0 + threadIdx.x + q * kPsThreads; },
+       [&](uint32_t dst, uint32_t v) { t.pbuf[1][dst] = v; });
+  if (expl) {
+    if (t.sid_bytes == 1)
+      pass([&](int q) { return sub[q]; }, [&](uint32_t dst, uint32_t v) { ((uint8_t*)t.sbuf[1])[dst] = (uint8_t)v; });
+    else
+      pass([&](int q) { return sub[q]; },
+           [&](uint32_t dst, uint32_t v) { ((uint16_t*)t.sbuf[1])[dst] = (uint16_t)v; });
+  }
 }
 
 // ------------------------------------------------------- widest spread
@@ -221,93 +361,44 @@ __global__ void k_pick_dim(const TreeDev* trees, StepDev s) {
 
 // ------------------------------------------------------------ segments
 
-// Per tile: points per subset -> seg_w (shared-memory histogram, then one
-// global atomic per non-empty subset of the tile).
-__global__ void __launch_bounds__(kTileThreads) k_seg_count(const TreeDev* trees, StepDev s) {
-  uint2 tl;
-  if (!tile_of(s, blockIdx.x, &tl)) return;
-  __shared__ uint32_t hist[kMaxSubsets];
-  const Cell cell = s.cells[tl.x];
-  const TreeDev& t = trees[cell.tree];
-  const int r = t.r;
-  const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
-  uint32_t sub[kItems];
-  load_subsets(t, src_sid(t, cell.level), src_perm(t, cell.level), cell.begin, tl.y, end, sub);
-  for (int j = threadIdx.x; j < r; j += blockDim.x) hist[j] = 0;
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < kItems; ++q)
-    if (sub[q] != 0xffffffffu) atomicAdd(&hist[sub[q]], 1u);
-  __syncthreads();
-  uint32_t* w = s.seg_w + s.seg_base[tl.x];
-  for (int j = threadIdx.x; j < r; j += blockDim.x)
-    if (hist[j]) atomicAdd(&w[j], hist[j]);
-}
-
-// One CTA per cell: segment start positions (exclusive scan over subsets) and
-// the list of segments too large for a single warp.
-__global__ void k_seg_scan(const TreeDev* trees, StepDev s) {
-  __shared__ uint32_t tmp[33];
+// One CTA per cell: the position range of every (cell, subset) segment from
+// the cell's subset offsets, and the list of segments too large for a single
+// warp. Offsets are clamped to the cell, so a damaged table cannot send a
+// later kernel outside it (it is reported instead).
+__global__ void k_segs(const TreeDev* trees, StepDev s) {
   const uint32_t c = blockIdx.x;
   const Cell cell = s.cells[c];
-  const int r = trees[cell.tree].r;
+  const TreeDev& t = trees[cell.tree];
+  const uint32_t r = (uint32_t)t.r;
+  const uint32_t* off = cell.level == 0 ? t.root_off : s.off_cur + s.obase_cur[c];
   const uint32_t g0 = s.seg_base[c];
-  uint32_t run = 0;
-  for (int j0 = 0; j0 < r; j0 += blockDim.x) {
-    const int j = j0 + threadIdx.x;
-    const uint32_t w = j < r ? s.seg_w[g0 + j] : 0u;
-    uint32_t tot;
-    const uint32_t ex = block_excl_scan(w, tmp, &tot);
-    if (j < r) {
-      const uint32_t beg = cell.begin + run + ex;
-      s.seg_beg[g0 + j] = beg;
-      s.seg_cur[g0 + j] = beg;
-      s.seg_cell[g0 + j] = c;
-      if (w > (uint32_t)kSelSmallMax) s.bigseg[atomicAdd(s.bigseg_count, 1u)] = g0 + j;
+  if (threadIdx.x == 0 && (off[0] != 0u || off[r] != cell.count)) set_status(t, ST_INTERNAL);
+  for (uint32_t j = threadIdx.x; j < r; j += blockDim.x) {
+    const uint32_t a = min(off[j], cell.count), b = min(off[j + 1], cell.count);
+    if (b < a) set_status(t, ST_INTERNAL);
+    const uint32_t w = b >= a ? b - a : 0u;
+    s.seg_beg[g0 + j] = cell.begin + a;
+    s.seg_w[g0 + j] = w;
+    s.seg_cell[g0 + j] = c;
+    if (w > (uint32_t)kSelSmallMax) {
+      const uint32_t k = atomicAdd(s.bigseg_count, 1u);
+      if (k < s.bigseg_cap) s.bigseg[k] = g0 + j; else set_status(t, ST_INTERNAL);
     }
-    run += tot;
   }
 }
 
-// Per tile: copy the keys of the tile's points into the scratch array grouped
-// by subset (order inside a segment is irrelevant to its median).
-__global__ void __launch_bounds__(kTileThreads) k_group(const TreeDev* trees, StepDev s) {
-  uint2 tl;
-  if (!tile_of(s, blockIdx.x, &tl)) return;
-  __shared__ uint32_t cnt[kMaxSubsets];
-  const Cell cell = s.cells[tl.x];
-  const TreeDev& t = trees[cell.tree];
-  const int r = t.r;
-  const float* X = src_cols(t, cell.level) + (int64_t)s.kdim[tl.x] * t.n + cell.begin;
-  const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
-  float x[kItems];
-#pragma unroll
-  for (int q = 0; q < kItems; ++q) {
-    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-    x[q] = i < end ? X[i] : 0.0f;
-  }
-  uint32_t sub[kItems];
-  load_subsets(t, src_sid(t, cell.level), src_perm(t, cell.level), cell.begin, tl.y, end, sub);
-  for (int j = threadIdx.x; j < r; j += blockDim.x) cnt[j] = 0;
-  __syncthreads();
-  uint32_t lr[kItems];
-#pragma unroll
-  for (int q = 0; q < kItems; ++q)
-    lr[q] = sub[q] != 0xffffffffu ? atomicAdd(&cnt[sub[q]], 1u) : 0u;
-  __syncthreads();
-  uint32_t* cur = s.seg_cur + s.seg_base[tl.x];
-  for (int j = threadIdx.x; j < r; j += blockDim.x)
-    if (cnt[j]) cnt[j] = atomicAdd(&cur[j], cnt[j]);  // now: base position of this tile's run
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < kItems; ++q)
-    if (sub[q] != 0xffffffffu) t.keys[cnt[sub[q]] + lr[q]] = ord_key(x[q]);
+// Key column of a cell (raw float bits; ord_key is applied on every load).
+__device__ __forceinline__ const uint32_t* key_column(const TreeDev& t, const Cell& cell, uint32_t dim) {
+  return (const uint32_t*)(src_cols(t, cell.level) + (int64_t)dim * t.n);
 }
+
+__device__ __forceinline__ uint32_t kload(const uint32_t* p) { return ord_key(__uint_as_float(__ldg(p))); }
 
 // ------------------------------------------------------------ selection
 
-// Exact key of 0-based rank `rank` among keys[0..w) by 8-bit MSD radix select,
-// one warp, histogram `hist` (256 words of shared memory owned by the warp).
+// Exact key of 0-based rank `rank` among the keys of raw[0..w) by 8-bit MSD
+// radix select, one warp, histogram `hist` (256 words of shared memory owned
+// by the warp).
 __device__ uint32_t warp_radix_select(const uint32_t* keys, uint32_t w, uint32_t rank, uint32_t* hist) {
   const int lane = threadIdx.x & 31;
   uint32_t prefix = 0, mask = 0;
@@ -316,14 +407,15 @@ __device__ uint32_t warp_radix_select(const uint32_t* keys, uint32_t w, uint32_t
     __syncwarp();
     uint32_t i = lane;
     for (; i + 96 < w; i += 128) {
-      const uint32_t k0 = keys[i], k1 = keys[i + 32], k2 = keys[i + 64], k3 = keys[i + 96];
+      const uint32_t k0 = kload(keys + i), k1 = kload(keys + i + 32), k2 = kload(keys + i + 64),
+                     k3 = kload(keys + i + 96);
       if ((k0 & mask) == prefix) atomicAdd(&hist[(k0 >> shift) & 255u], 1u);
       if ((k1 & mask) == prefix) atomicAdd(&hist[(k1 >> shift) & 255u], 1u);
       if ((k2 & mask) == prefix) atomicAdd(&hist[(k2 >> shift) & 255u], 1u);
       if ((k3 & mask) == prefix) atomicAdd(&hist[(k3 >> shift) & 255u], 1u);
     }
     for (; i < w; i += 32) {
-      const uint32_t k = keys[i];
+      const uint32_t k = kload(keys + i);
       if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
     }
     __syncwarp();
@@ -340,7 +432,7 @@ __device__ uint32_t warp_radix_select(const uint32_t* keys, uint32_t w, uint32_t
 // Lower median of one small segment (w <= 32) by counting ranks in registers.
 __device__ __forceinline__ uint32_t warp_rank_median(const uint32_t* keys, uint32_t w) {
   const int lane = threadIdx.x & 31;
-  const uint32_t k = (uint32_t)lane < w ? keys[lane] : 0xffffffffu;
+  const uint32_t k = (uint32_t)lane < w ? kload(keys + lane) : 0xffffffffu;
   const uint32_t want = (w - 1) / 2;
   uint32_t rk = 0;
   for (uint32_t j = 0; j < w; ++j) {
@@ -360,8 +452,9 @@ __global__ void __launch_bounds__(256) k_select_small(const TreeDev* trees, Step
   for (uint32_t g = blockIdx.x * 8u + (uint32_t)warp; g < nseg; g += gridDim.x * 8u) {
     const uint32_t w = s.seg_w[g];
     if (w == 0 || w > (uint32_t)kSelSmallMax) continue;
-    const Cell cell = s.cells[s.seg_cell[g]];
-    const uint32_t* keys = trees[cell.tree].keys + s.seg_beg[g];
+    const uint32_t c = s.seg_cell[g];
+    const Cell cell = s.cells[c];
+    const uint32_t* keys = key_column(trees[cell.tree], cell, s.kdim[c]) + s.seg_beg[g];
     uint32_t med;
     if (w <= 32)
       med = warp_rank_median(keys, w);
@@ -379,8 +472,9 @@ __global__ void __launch_bounds__(256) k_select_big(const TreeDev* trees, StepDe
   __shared__ uint32_t bcast[2];
   const uint32_t g = s.bigseg[blockIdx.x];
   const uint32_t w = s.seg_w[g];
-  const Cell cell = s.cells[s.seg_cell[g]];
-  const uint32_t* keys = trees[cell.tree].keys + s.seg_beg[g];
+  const uint32_t c = s.seg_cell[g];
+  const Cell cell = s.cells[c];
+  const uint32_t* keys = key_column(trees[cell.tree], cell, s.kdim[c]) + s.seg_beg[g];
   uint32_t rank = (w - 1) / 2, prefix = 0, mask = 0;
   for (int shift = 24; shift >= 0; shift -= 8) {
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
@@ -389,13 +483,13 @@ __global__ void __launch_bounds__(256) k_select_big(const TreeDev* trees, StepDe
     for (; i + 7 * 256 < w; i += 8 * 256) {
       uint32_t k[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) k[q] = keys[i + q * 256];
+      for (int q = 0; q < 8; ++q) k[q] = kload(keys + i + q * 256);
 #pragma unroll
       for (int q = 0; q < 8; ++q)
         if ((k[q] & mask) == prefix) atomicAdd(&hist[(k[q] >> shift) & 255u], 1u);
     }
     for (; i < w; i += 256) {
-      const uint32_t k = keys[i];
+      const uint32_t k = kload(keys + i);
       if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
     }
     __syncthreads();
@@ -543,8 +637,11 @@ __global__ void k_child_mm(const TreeDev* trees, StepDev s) {
 
 // ------------------------------------------------------------- children
 
-// One thread per cell: classify the two children.
-__global__ void k_next(const TreeDev* trees, StepDev s) {
+// One thread per cell, after the children's sizes are known and before the
+// move: terminal children are recorded, small ones queued for the subtree
+// kernel, big ones get a slot of the next step and a row of its subset
+// offsets (which the scatter fills).
+__global__ void k_classify(const TreeDev* trees, StepDev s) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= s.ncells) return;
   const Cell cell = s.cells[c];
@@ -556,62 +653,87 @@ __global__ void k_next(const TreeDev* trees, StepDev s) {
   const uint32_t cc[2] = {L, R};
   int live_delta = -1;  // this cell is done; each child that still needs splitting adds one
   for (int side = 0; side < 2; ++side) {
+    uint2 cr = make_uint2(kNoRow, kNoRow);
     const uint32_t heap = 2u * cell.heap + 1u + (uint32_t)side;
     if (is_terminal(t, cc[side], level, stall)) {
       record_terminal(t, cb[side], cc[side], heap, level);
-      continue;
-    }
-    if (t.depth == 0 && level >= t.max_levels) {
+    } else if (t.depth == 0 && level >= t.max_levels) {
       set_status(t, ST_LEVEL_CAP);
-      continue;
-    }
-    ++live_delta;
-    int16_t dim = -1;
-    if (t.key_rule == KEY_WIDEST) {
-      int best = 0;
-      double best_range = -1.0;
-      for (int l = 0; l < t.d; ++l) {
-        const double range = key_range(s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 0],
-                                       s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 1]);
-        if (range > best_range) {
-          best_range = range;
-          best = l;
-        }
-      }
-      dim = (int16_t)best;
-    }
-    const Cell child{cb[side], cc[side], heap, cell.tree, (int8_t)level, (int8_t)stall, dim};
-    if (cc[side] <= (uint32_t)t.small_max) {
-      const uint32_t slot = atomicAdd(s.small_count, 1u);
-      if (slot < s.small_cap) s.small[slot] = child; else set_status(t, ST_CAPACITY);
-      atomicAdd(s.small_points, cc[side]);
     } else {
-      const uint32_t slot = atomicAdd(s.next_big_count, 1u);
-      if (slot < s.next_big_cap) s.next_big[slot] = child; else set_status(t, ST_CAPACITY);
-      atomicAdd(s.next_big_points, cc[side]);
+      ++live_delta;
+      const Cell child{cb[side], cc[side], heap, cell.tree, (int8_t)level, (int8_t)stall, (int16_t)-1};
+      if (cc[side] <= (uint32_t)t.small_max) {
+        const uint32_t slot = atomicAdd(s.small_count, 1u);
+        if (slot < s.small_cap) s.small[slot] = child; else set_status(t, ST_CAPACITY);
+        atomicAdd(s.small_points, cc[side]);
+      } else {
+        const uint32_t slot = atomicAdd(s.next_big_count, 1u);
+        const uint32_t row = atomicAdd(s.off_used, (uint32_t)t.r + 1u);
+        if (slot < s.next_big_cap && row <= s.off_cap - ((uint32_t)t.r + 1u)) {
+          s.next_big[slot] = child;
+          s.obase_next[slot] = row;
+          cr = make_uint2(slot, row);
+        } else {
+          set_status(t, ST_CAPACITY);
+        }
+        atomicAdd(s.next_big_points, cc[side]);
+      }
     }
+    s.crow[2 * c + side] = cr;
   }
   if (live_delta) atomicAdd(t.live, live_delta);
+}
+
+// One thread per cell (widest spread): the key coordinate of each big child
+// from the min and max keys the scatter reduced for it.
+__global__ void k_next_dims(const TreeDev* trees, StepDev s) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= s.ncells) return;
+  const Cell cell = s.cells[c];
+  const TreeDev& t = trees[cell.tree];
+  if (t.key_rule != KEY_WIDEST) return;
+  for (int side = 0; side < 2; ++side) {
+    const uint2 cr = s.crow[2 * c + side];
+    if (cr.x == kNoRow) continue;
+    int best = 0;
+    double best_range = -1.0;
+    for (int l = 0; l < t.d; ++l) {
+      const double range = key_range(s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 0],
+                                     s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 1]);
+      if (range > best_range) {
+        best_range = range;
+        best = l;
+      }
+    }
+    s.next_big[cr.x].dim = (int16_t)best;
+  }
 }
 
 }  // namespace
 
 // ------------------------------------------------------------ launcher
 
+cudaError_t prepare_step_kernels() {
+  return cudaFuncSetAttribute(k_ps_move, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPsSmemBytes);
+}
+
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
-                     uint32_t max_bigseg, bool need_root_dims, bool any_widest, int max_d, uint64_t points,
-                     uint32_t sms, cudaStream_t st) {
+                     uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d,
+                     uint64_t points, uint32_t sms, cudaStream_t st) {
   const uint32_t nc = s.ncells;
   if (nc == 0) return;
   { TraceScope ts(K_PREP, st); k_prep<<<1, 1024, 0, st>>>(trees, s); }
-  { TraceScope ts(K_TILES, st); k_tiles<<<nc, 256, 0, st>>>(s); }
+  { TraceScope ts(K_TILES, st); k_tiles<<<nc, 256, 0, st>>>(trees, s); }
+  if (has_roots) {
+    { TraceScope ts(K_PS_COUNT, st, points); k_ps_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
+    { TraceScope ts(K_PS_OFFSETS, st); k_ps_offsets<<<nc, 1024, 0, st>>>(trees, s); }
+    { TraceScope ts(K_PS_MOVE, st, points); k_ps_move<<<max_tiles, kPsThreads, kPsSmemBytes, st>>>(trees, s); }
+  }
+  { TraceScope ts(K_SEGS, st); k_segs<<<nc, 256, 0, st>>>(trees, s); }
   if (need_root_dims) {
     { TraceScope ts(K_MINMAX, st, points); k_minmax<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
     { TraceScope ts(K_PICK_DIM, st); k_pick_dim<<<nc, 256, 0, st>>>(trees, s); }
   }
-  { TraceScope ts(K_SEG_COUNT, st, points); k_seg_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
-  { TraceScope ts(K_SEG_SCAN, st); k_seg_scan<<<nc, 256, 0, st>>>(trees, s); }
-  { TraceScope ts(K_GROUP, st, points); k_group<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
   {
     TraceScope ts(K_SELECT_SMALL, st, points);
     k_select_small<<<std::min<uint32_t>((nseg + 7) / 8, 152u * 32u), 256, 0, st>>>(trees, s);
@@ -620,12 +742,12 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
   { TraceScope ts(K_COMBINE, st); k_combine<<<nc, 256, 0, st>>>(trees, s); }
   { TraceScope ts(K_PART_COUNT, st, points); k_part_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
   { TraceScope ts(K_PART_SCAN, st); k_part_scan<<<nc, 1024, 0, st>>>(s); }
+  { TraceScope ts(K_CLASSIFY, st); k_classify<<<(nc + 255) / 256, 256, 0, st>>>(trees, s); }
   launch_scatter(trees, s, max_tiles, 2 * sms, points, st);
   if (any_widest) {
-    TraceScope ts(K_CHILD_MM, st);
-    k_child_mm<<<dim3(nc, 2, max_d), 256, 0, st>>>(trees, s);
+    { TraceScope ts(K_CHILD_MM, st); k_child_mm<<<dim3(nc, 2, max_d), 256, 0, st>>>(trees, s); }
+    { TraceScope ts(K_NEXT_DIMS, st); k_next_dims<<<(nc + 255) / 256, 256, 0, st>>>(trees, s); }
   }
-  { TraceScope ts(K_NEXT, st); k_next<<<(nc + 255) / 256, 256, 0, st>>>(trees, s); }
 }
 
 }  // namespace kdt

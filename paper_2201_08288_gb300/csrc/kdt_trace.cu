@@ -1,5 +1,7 @@
 // kdt_trace.cu -- launch counter and per-kernel event timing (see kdt_trace.h).
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -10,9 +12,11 @@ namespace kdt {
 namespace {
 
 const char* const kNames[K_NUM] = {
-    "k_prep", "k_tiles", "k_minmax", "k_pick_dim", "k_seg_count", "k_seg_scan", "k_group",
-    "k_select_small", "k_select_big", "k_combine", "k_part_count", "k_part_scan", "k_part_scatter",
-    "k_child_mm", "k_next", "k_subtree", "k_finalize", "k_iota", "k_batch_seed"};
+    "k_prep",       "k_tiles",      "k_ps_count",   "k_ps_offsets",  "k_ps_move",     "k_segs",
+    "k_minmax",     "k_pick_dim",   "k_select_small", "k_select_big", "k_combine",    "k_part_count",
+    "k_part_scan",  "k_classify",   "k_part_scatter", "k_child_mm",   "k_next_dims",  "k_subtree",
+    "k_finalize",   "k_iota",       "k_leaf_sort",  "k_leaf_hist",   "k_leaf_scan",   "k_leaf_scatter",
+    "k_leaf_copy"};
 
 struct Pending {
   KernelId id;
@@ -51,6 +55,16 @@ TraceScope::TraceScope(KernelId id, cudaStream_t st, uint64_t units) : id_(id), 
 }
 
 TraceScope::~TraceScope() {
+  // KDT_SYNC_CHECK=1: synchronise after every launch and name the kernel of
+  // the first error (a debugging aid; off by default)
+  static const bool sync_check = [] {
+    const char* v = std::getenv("KDT_SYNC_CHECK");
+    return v && *v && *v != '0';
+  }();
+  if (sync_check) {
+    const cudaError_t e = cudaStreamSynchronize(st_);
+    if (e != cudaSuccess) std::fprintf(stderr, "kdt: %s: %s\n", kNames[id_], cudaGetErrorString(e));
+  }
   if (!start_) return;
   cudaEvent_t stop = nullptr;
   if (cudaEventCreate(&stop) != cudaSuccess) {
