@@ -82,8 +82,9 @@ TreePlan plan_tree(const kdt_params& p) {
   t.small_max = subtree_capacity(p.d);
   t.sid_bytes = p.subset_mode == KDT_SUBSET_EXPLICIT ? (p.subset_id16 ? 2 : 1) : 0;
   const bool root_terminal = p.depth > 0 ? (n == 0) : (n <= (uint64_t)p.leaf_size);
-  t.presorted = !root_terminal && n > (uint64_t)t.small_max && p.subset_mode != KDT_SUBSET_CONTIGUOUS;
-  t.huge_cap = t.presorted ? n / (uint64_t)(kLeafBlockMax + 1) + 1 : 0;
+  t.leafsort = !root_terminal && p.subset_mode != KDT_SUBSET_CONTIGUOUS;
+  t.presorted = t.leafsort && n > (uint64_t)t.small_max;
+  t.huge_cap = t.leafsort ? n / (uint64_t)(kLeafBlockMax + 1) + 1 : 0;
   const uint64_t leaves = (uint64_t)1 << t.L_cap;
   t.maxB = std::min<uint64_t>(n / (uint64_t)(t.small_max + 1) + 1, leaves);
   t.cap_small = std::min<uint64_t>(n, leaves) + 1;
@@ -130,7 +131,7 @@ StepPlan plan_step(const StepNeeds& needs) {
   s.off_cap = (uint32_t)std::min<uint64_t>(needs.nseg + needs.maxB, clamp);
   s.bigseg_cap = (uint32_t)std::min<uint64_t>(needs.points / (kSelSmallMax + 1) + 1, clamp);
   const int sms = device_sms();
-  s.grid_sub = (uint32_t)(sms > 0 ? sms : 148);
+  s.grid_sub = (uint32_t)(sms > 0 ? sms : 148) * (uint32_t)kSubtreeCtasPerSm;
   const uint32_t mt = std::max<uint32_t>(needs.max_trees, 1);
   size_t off = 0;
   auto take = [&](size_t b) {
@@ -215,7 +216,7 @@ Engine::Engine(const StepPlan& plan, uint8_t* base, cudaStream_t st) : plan_(pla
   s_.crow = (uint2*)(base + plan.crow);
   const uint32_t mt = std::max<uint32_t>(plan.needs.max_trees, 1);
   host_.assign(mt, TreeHost{});
-  presorted_.assign(mt, 0);
+  leafsort_.assign(mt, 0);
 }
 
 kdt_status Engine::reset() {
@@ -277,7 +278,7 @@ kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p
   for (int w = 0; w < S_COUNT; ++w)
     ENGINE_TRY(cudaMemsetAsync(slot_words_ + (size_t)w * mt + slot, 0, 4, st_));
   ENGINE_TRY(cudaMemsetAsync(h.huge_count, 0, 4, st_));
-  presorted_[slot] = tp.presorted ? 1 : 0;
+  leafsort_[slot] = tp.leafsort ? 1 : 0;
   // after the build the tree's working buffers are free: the global leaf-sort
   // passes use pbuf[0] as their second buffer and xbuf[0] for tile tables
   host_[slot] = TreeHost{(uint64_t)p.n, out_perm, h.pbuf[0], (void*)h.xbuf[0], (size_t)p.d * p.n * 4};
@@ -408,9 +409,9 @@ kdt_status Engine::finalize(const std::vector<uint32_t>& slots, std::vector<kdt_
       ok.push_back(s);
       max_rec = std::max(max_rec, tc[s]);
     }
-  std::vector<uint32_t> sorted;  // presorted trees: their leaves need the leaf sort
+  std::vector<uint32_t> sorted;  // trees kept in subset order: their leaves need the leaf sort
   for (uint32_t s : ok)
-    if (presorted_[s]) sorted.push_back(s);
+    if (leafsort_[s]) sorted.push_back(s);
   if (!ok.empty()) {
     ENGINE_TRY(cudaMemcpyAsync(slots_list_, ok.data(), ok.size() * 4, cudaMemcpyHostToDevice, st_));
     launch_finalize_many(trees_, slots_list_, (uint32_t)ok.size(), max_rec, st_);

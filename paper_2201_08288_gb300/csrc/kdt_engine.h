@@ -27,6 +27,7 @@ struct TreePlan {
   int small_max = 0;
   int sid_bytes = 0;
   bool presorted = false;  // big root and subsets not already in index order
+  bool leafsort = false;   // subsets not in index order: leaves are sorted at the end
   uint64_t n = 0;
   uint64_t term_cap = 0;
   uint64_t huge_cap = 0;  // terminal cells larger than one CTA's leaf sort
@@ -101,7 +102,7 @@ class Engine {
   bool debug_ = false;
   std::vector<Cell> pending_big_, pending_small_;
   std::vector<TreeHost> host_;       // per slot: leaf-sort view of a presorted tree
-  std::vector<uint8_t> presorted_;   // per slot
+  std::vector<uint8_t> leafsort_;    // per slot
 };
 
 }  // namespace kdt

@@ -30,8 +30,7 @@ constexpr int kMaxLevels = 30;        // depth / max_levels <= 30
 constexpr int kTile = 2048;           // points per tile of the multi-CTA pipeline
 constexpr int kTileThreads = 256;     // threads of the tile kernels
 constexpr int kSelSmallMax = 4096;    // segments up to this size: one warp per segment
-constexpr int kSubtreeThreads = 512;  // threads of the in-shared-memory subtree kernel
-constexpr int kSubtreeBins = 4096;    // (cell, subset) bins per batch in the subtree kernel
+constexpr int kSubtreeThreads = 256;  // threads of a CTA of the in-shared-memory subtree kernel
 constexpr int kSubtreeWarps = kSubtreeThreads / 32;
 
 // status codes (mirror include/kdt.h)
@@ -310,6 +309,91 @@ __device__ __forceinline__ uint32_t warp_find_digit(const uint32_t* hist, uint32
   digit = __shfl_sync(0xffffffffu, digit, owner);
   *below = __shfl_sync(0xffffffffu, b, owner);
   return digit;
+}
+
+// Like warp_find_digit for a histogram of nb = 2^bits bins (1 <= bits <= 8).
+__device__ __forceinline__ uint32_t warp_find_digit_n(const uint32_t* hist, uint32_t nb, uint32_t rank,
+                                                      uint32_t* below) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t per = nb >= 32u ? nb / 32u : 1u;
+  const uint32_t first = lane * per;
+  uint32_t local[8];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    local[i] = ((uint32_t)i < per && first + i < nb) ? hist[first + i] : 0u;
+    s += local[i];
+  }
+  const uint32_t incl = warp_incl_scan(s);
+  const uint32_t excl = incl - s;
+  const unsigned ballot = __ballot_sync(0xffffffffu, rank >= excl && rank < incl);
+  const int owner = ballot ? __ffs(ballot) - 1 : 31;
+  uint32_t digit = 0, b = 0;
+  if (lane == owner) {
+    uint32_t acc = excl;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if ((uint32_t)i < per && rank < acc + local[i]) {
+        digit = first + i;
+        b = acc;
+        break;
+      }
+      acc += local[i];
+    }
+  }
+  digit = __shfl_sync(0xffffffffu, digit, owner);
+  *below = __shfl_sync(0xffffffffu, b, owner);
+  return digit;
+}
+
+// Exact key of 0-based weighted rank `rank` among cnt items (key_of(j),
+// w_of(j)), j < cnt, one warp: the smallest key m whose items with key <= m
+// weigh more than `rank`. MSD radix select over the bits where the keys
+// differ (the common prefix of their min and max is known from the start, so
+// no pass is spent on bits every key shares), 8-bit digits, histogram `hist`
+// of 256 words owned by the warp.
+template <bool kUnit = false, class KeyOf, class WOf, class ValidOf>
+__device__ uint32_t warp_weighted_select(uint32_t cnt, uint32_t rank, uint32_t* hist, KeyOf key_of, WOf w_of,
+                                         ValidOf valid_of) {
+  const int lane = threadIdx.x & 31;
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  for (uint32_t j = lane; j < cnt; j += 32)
+    if (valid_of(j)) {
+      const uint32_t k = key_of(j);
+      lo = min(lo, k);
+      hi = max(hi, k);
+    }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if (lo >= hi) return lo;
+  int rem = 32 - __clz(lo ^ hi);  // low bits still unknown
+  uint32_t prefix = rem == 32 ? 0u : (lo & ~((1u << rem) - 1u));
+  while (rem > 0) {
+    const int bits = rem < 8 ? rem : 8;
+    const int shift = rem - bits;
+    const uint32_t nb = 1u << bits;
+    const uint32_t hmask = rem == 32 ? 0u : ~((1u << rem) - 1u);
+    for (uint32_t i = lane; i < nb; i += 32) hist[i] = 0;
+    __syncwarp();
+    for (uint32_t j = lane; j < cnt; j += 32) {
+      if (!valid_of(j)) continue;
+      const uint32_t k = key_of(j);
+      if ((k & hmask) == prefix) atomicAdd(&hist[(k >> shift) & (nb - 1u)], kUnit ? 1u : w_of(j));
+    }
+    __syncwarp();
+    uint32_t below;
+    const uint32_t digit = warp_find_digit_n(hist, nb, rank, &below);
+    rank -= below;
+    prefix |= digit << shift;
+    rem = shift;
+    __syncwarp();
+  }
+  return prefix;
+}
+
+template <bool kUnit = false, class KeyOf, class WOf>
+__device__ uint32_t warp_weighted_select(uint32_t cnt, uint32_t rank, uint32_t* hist, KeyOf key_of, WOf w_of) {
+  return warp_weighted_select<kUnit>(cnt, rank, hist, key_of, w_of, [](uint32_t) { return true; });
 }
 
 // Block-wide exclusive scan of one value per thread; returns the exclusive

@@ -22,13 +22,15 @@ struct LCell {
 };
 static_assert(sizeof(LCell) == 16, "LCell is 16 bytes");
 
-// Shared-memory budget of the subtree kernel.
-constexpr size_t kSubtreeSmemBytes = 231424;  // dynamic part
-constexpr int kSubtreeBigBinCap = 1024;
-constexpr int kSubtreeSmemCells = 512;
-constexpr size_t kSubtreeFixedBytes =
-    16400 /* bins */ + (size_t)kSubtreeBins * 4 /* medians */ + (size_t)kSubtreeWarps * 256 * 4 +
-    (size_t)kSubtreeBigBinCap * 2 + 2 * (size_t)kSubtreeSmemCells * sizeof(LCell);
+// Shared-memory budget of the subtree kernel: kSubtreeCtasPerSm CTAs share an
+// SM, each finishing its own cell, so that one CTA's barriers and copies
+// overlap the other's work.
+constexpr int kSubtreeCtasPerSm = 2;
+constexpr size_t kSubtreeSmemBytes = 112 * 1024;  // dynamic part, per CTA
+constexpr int kSubtreeBigCap = 1024;              // segments above the rank-counting size
+constexpr int kSubtreeSmemCells = 256;
+constexpr size_t kSubtreeFixedBytes = (size_t)kSubtreeWarps * 256 * 4 /* warp histograms */ +
+                                      (size_t)kSubtreeBigCap * 2 + 2 * (size_t)kSubtreeSmemCells * sizeof(LCell);
 
 // Column stride (elements) of a cell of N points in shared memory: room for
 // the 16-byte alignment phase of the bulk copies.
@@ -36,12 +38,13 @@ __host__ __device__ inline uint32_t subtree_stride(uint32_t N) { return (N + 8 +
 
 // Bytes of shared memory a cell of N points with d coordinates needs beyond
 // the fixed part: d key columns and the permutation at the padded stride, the
-// gathered keys (4 bytes), the subset ids, two orders, cell ids, the scan and
-// the bin / flag array (2 bytes each).
+// keys in local order and the segment medians (4 bytes each), the subset ids,
+// two orders, cell ids, a scan, the segment starts and a flag array (2 bytes
+// each).
 __host__ __device__ inline size_t subtree_point_bytes(uint32_t N, int d) {
   const size_t stride = subtree_stride(N);
-  return (size_t)(d + 1) * stride * 4 + (((size_t)N * 4 + 15) & ~(size_t)15) +
-         6 * ((((size_t)N + 1) * 2 + 15) & ~(size_t)15);
+  return (size_t)(d + 1) * stride * 4 + 2 * (((size_t)N * 4 + 15) & ~(size_t)15) +
+         7 * ((((size_t)N + 1) * 2 + 15) & ~(size_t)15);
 }
 
 // Largest cell (points) the subtree kernel holds for d coordinates.

@@ -5,10 +5,13 @@
 
 namespace kdt {
 
-// Iterations of a bounded mbarrier wait (each try_wait also suspends the
-// thread for a hardware-chosen interval), after which the caller reports a
-// timeout instead of spinning forever.
-constexpr uint32_t kSpinLimit = 1u << 22;
+// Iterations of a bounded mbarrier wait, after which the caller reports a
+// timeout instead of waiting forever. Each try_wait may suspend the thread
+// for up to kWaitHintNs (it resumes when the phase completes), so waiting
+// warps do not take issue slots from working ones; the bound is about
+// kSpinLimit * kWaitHintNs = 2 s.
+constexpr uint32_t kSpinLimit = 1u << 20;
+constexpr uint32_t kWaitHintNs = 2000;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -56,10 +59,23 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// try_wait that may suspend the thread for up to `ns` nanoseconds.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t phase, uint32_t ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(phase), "r"(ns)
+      : "memory");
+  return done != 0;
+}
+
 // Bounded wait on an mbarrier phase: false if it did not complete in time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
   for (uint32_t it = 0; it < kSpinLimit; ++it)
-    if (mbar_try_wait(bar, phase)) return true;
+    if (mbar_try_wait_hint(bar, phase, kWaitHintNs)) return true;
   return false;
 }
 

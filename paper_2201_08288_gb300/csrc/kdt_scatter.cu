@@ -4,23 +4,26 @@
 // For every tile of a big cell (paper, Sec. 2: after a cell's split, its
 // points go to the two children; ties go left), in sub-tiles of T points:
 //   producer warp (warp 8): waits until one of two shared-memory buffers is
-//     free ("empty" mbarrier), copies the sub-tile's metadata and its tree's
-//     descriptor into shared memory, raises the buffer's expected byte count,
-//     starts bulk copies (cp.async.bulk) of the aligned middle of every
-//     coordinate column and of the permutation, copies the ragged 16-byte
-//     edges with 4-byte cp.async (tracked by the same mbarrier), and arrives
-//     on the buffer's "full" mbarrier; the next tile's record is loaded one
-//     tile ahead;
+//     free ("empty" mbarrier), writes the sub-tile's metadata (output
+//     pointers, which children are terminal, what to compute), raises the
+//     buffer's expected byte count, starts bulk copies (cp.async.bulk) of
+//     the aligned middle of every coordinate column, of the permutation and
+//     of the subset ids, copies the ragged 16-byte edges (4-byte cp.async for
+//     word columns, plain loads for the ids) and arrives on the buffer's
+//     "full" mbarrier; the next tile's record is loaded one tile ahead;
 //   consumer warps (0-7): wait for "full" (bounded), compute each point's
 //     left/right flag from its key and its rank by warp ballots in position
 //     order (so the partition is stable), store every value straight from
-//     shared memory to its destination, and release the buffer.
+//     shared memory to its destination, two columns at a time, and release
+//     the buffer.
 // A child that is terminal receives only its permutation, in out_perm. For
 // widest spread the consumers also reduce each child's min and max key per
-// coordinate. Points of a cell arrive in subset order (contiguous segments),
-// and a stable partition keeps that order in both children; where the subset
-// changes, the consumers write where each big child's segments start (its
-// left or right rank there), which is the children's subset offset table.
+// coordinate (per warp, then one shared-memory reduction per warp and
+// column, fire-and-forget). Points of a cell arrive in subset order
+// (contiguous segments), and a stable partition keeps that order in both
+// children; where the subset changes, the consumers write where each big
+// child's segments start (its left or right rank there), which is the
+// children's subset offset table.
 #include <algorithm>
 
 #include "kdt_internal.cuh"
@@ -39,23 +42,35 @@ constexpr int kMaxItems = 4;          // points per consumer thread in a sub-til
 constexpr uint32_t kBufBytes = kScatterSmemBytes / 2;
 constexpr uint32_t kConsumerBar = 1;  // named barrier of the consumer warps
 
-// Largest power-of-two sub-tile whose ncols columns (stride T + 4 words)
-// fit one buffer.
-__device__ __forceinline__ uint32_t sub_tile(int ncols) {
+// Largest power-of-two sub-tile whose ncols word columns (stride T + 4) and
+// an id column of sid_bytes per point (T + 32 entries) fit one buffer.
+__device__ __forceinline__ uint32_t sub_tile(int ncols, int sid_bytes) {
   uint32_t T = 1024;
-  while (T > 32 && (uint32_t)ncols * (T + 4) * 4u > kBufBytes) T >>= 1;
+  while (T > 32 && (uint32_t)ncols * (T + 4) * 4u + (T + 32) * (uint32_t)sid_bytes > kBufBytes) T >>= 1;
   return T;
 }
 
 // What the consumers need about the sub-tile in a buffer.
 struct SubMeta {
-  TreeDev t;
-  Cell cell;
-  uint32_t tile, sub, mcnt, T, dim, mkey, L, loff, tile_start;
-  uint32_t row[2];            // rows of the children's subset offsets (kNoRow: not a big child)
-  uint32_t prev_sub;          // subset of the point before the sub-tile (~0u at the cell's start)
-  uint32_t ph[kMaxDims + 1];  // alignment phase of each staged column
+  float* xout;         // coordinate columns of the next level
+  uint32_t* pout;      // permutation of the next level
+  void* sout;          // subset ids of the next level (explicit ids)
+  uint32_t* out_perm;  // final permutation (terminal children)
+  int32_t* status;
+  int64_t n;
+  uint32_t cell_begin, cell_count, tile, sub, mcnt, T, dim, mkey, L, loff, tile_start;
+  uint32_t row[2];     // rows of the children's subset offsets (kNoRow: not a big child)
+  uint32_t prev_sub;   // subset of the point before the sub-tile (~0u at the cell's start)
+  uint32_t r, subset_mode, sid_bytes, sid_ph, tn;
+  int32_t d;
+  uint8_t term_left, term_right, want_mm, want_off, level0, pad0, pad1, pad2;
+  uint32_t ph[kMaxDims + 1];  // alignment phase of each staged word column
 };
+
+__device__ __forceinline__ uint32_t meta_subset(const SubMeta& m, uint32_t orig) {
+  if (m.subset_mode == SUB_MOD) return orig % m.r;
+  return (uint32_t)(((uint64_t)orig * (uint64_t)m.r) / (uint64_t)m.tn);
+}
 
 __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, StepDev s) {
   extern __shared__ __align__(128) uint32_t sm[];
@@ -63,7 +78,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
   __shared__ SubMeta meta[2];
   __shared__ uint32_t wcnt[kMaxItems][kCW];
   __shared__ uint32_t sedge[kMaxItems][kCW];  // subset of each warp's last point per round
-  __shared__ uint32_t wmm[kCW][2][kMaxDims][2];
+  __shared__ uint32_t tmm[2][kMaxDims][2];    // per tile and child: min / max key per coordinate
   __shared__ uint32_t s_fail;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ntiles = *s.ntiles_total;
@@ -93,12 +108,18 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       }
       const TreeDev& tg = trees[c.tree];
       const int d = tg.d, ncols = d + 1;
-      const uint32_t T = sub_tile(ncols), stride = T + 4;
+      const bool expl = tg.subset_mode == SUB_EXPLICIT;
+      const int es = expl ? tg.sid_bytes : 0;
+      const uint32_t T = sub_tile(ncols, es), stride = T + 4;
       const uint32_t tend = min(tl.y + (uint32_t)kTile, c.count);
       const float* X = src_cols(tg, c.level);
       const uint32_t* P = src_perm(tg, c.level);
+      const uint8_t* SID = (const uint8_t*)src_sid(tg, c.level);
       const uint32_t dim = s.kdim[tl.x], mkey = s.mkey[tl.x], L = s.lcount[tl.x], loff = s.tile_loff[tile];
       const uint2 cr0 = s.crow[2 * tl.x], cr1 = s.crow[2 * tl.x + 1];
+      const int child_stall = (c.count == L) ? c.stall + 1 : 0;
+      const bool term_left = is_terminal(tg, L, c.level + 1, child_stall);
+      const bool term_right = is_terminal(tg, c.count - L, c.level + 1, child_stall);
       for (uint32_t sub = tl.y; sub < tend; sub += T, ++k) {
         const int b = k & 1;
         if (k >= 2) {
@@ -112,11 +133,25 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         const uint32_t mcnt = min(T, tend - sub);
         const uint32_t g0 = c.begin + sub;
         SubMeta& m = meta[b];
-        // tree descriptor and sub-tile metadata
-        for (uint32_t w = lane; w < sizeof(TreeDev) / 4; w += 32)
-          ((uint32_t*)&m.t)[w] = ((const uint32_t*)&tg)[w];
+        uint32_t* A = sm + (size_t)b * (kBufBytes / 4);
+        uint8_t* SA = (uint8_t*)(A + (size_t)ncols * stride);  // 16-byte aligned (stride * 4 is)
+        // id column: 16-byte phase in elements, aligned middle [sa0, sa1)
+        uint32_t sph = 0, sa0 = g0, sa1 = g0;
+        if (expl) {
+          const uint32_t per16 = 16u / (uint32_t)es;
+          sph = (uint32_t)(((uintptr_t)(SID + (size_t)g0 * es) / (uintptr_t)es) & (per16 - 1u));
+          sa0 = min(g0 + ((per16 - sph) & (per16 - 1u)), g0 + mcnt);
+          sa1 = sa0 + ((g0 + mcnt - sa0) & ~(per16 - 1u));
+        }
         if (lane == 0) {
-          m.cell = c;
+          m.xout = tg.xbuf[c.level & 1];
+          m.pout = tg.pbuf[c.level & 1];
+          m.sout = tg.sbuf[c.level & 1];
+          m.out_perm = tg.out_perm;
+          m.status = tg.status;
+          m.n = tg.n;
+          m.cell_begin = c.begin;
+          m.cell_count = c.count;
           m.tile = tile;
           m.sub = sub;
           m.mcnt = mcnt;
@@ -131,9 +166,19 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           m.prev_sub = (sub > 0u && (cr0.x != kNoRow || cr1.x != kNoRow))
                            ? subset_at(tg, c.level, (int64_t)g0 - 1)
                            : 0xffffffffu;
+          m.r = (uint32_t)tg.r;
+          m.subset_mode = (uint32_t)tg.subset_mode;
+          m.sid_bytes = (uint32_t)es;
+          m.sid_ph = sph;
+          m.tn = (uint32_t)tg.n;
+          m.d = d;
+          m.term_left = term_left;
+          m.term_right = term_right;
+          m.want_mm = tg.key_rule == KEY_WIDEST && !(term_left && term_right);
+          m.want_off = cr0.x != kNoRow || cr1.x != kNoRow;
+          m.level0 = c.level == 0;
         }
-        uint32_t* A = sm + (size_t)b * (kBufBytes / 4);
-        uint32_t total = 0;
+        uint32_t total = expl ? (sa1 - sa0) * (uint32_t)es : 0u;
         for (int c0 = 0; c0 < ncols; c0 += 32) {
           const int col = c0 + lane;
           uint32_t bytes = 0;
@@ -155,7 +200,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           const int col = c0 + lane;
           if (col >= ncols) continue;
           const uint32_t* src = col < d ? (const uint32_t*)(X + (int64_t)col * tg.n) : P;
-          if (!src) continue;  // level 0: the identity permutation, filled below
+          if (!src) continue;  // level 0 without a presort: the identity permutation, filled below
           uint32_t* dst = A + (size_t)col * stride;
           const uint32_t ph = (uint32_t)(((uintptr_t)(src + g0) >> 2) & 3u);
           const uint32_t a0 = min(g0 + ((4u - ph) & 3u), g0 + mcnt);
@@ -163,6 +208,20 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           if (a1 > a0) bulk_g2s(dst + ph + (a0 - g0), src + a0, (a1 - a0) * 4u, &full[b]);
           for (uint32_t idx = g0; idx < a0; ++idx) cp_async4(dst + ph + (idx - g0), src + idx);
           for (uint32_t idx = a1; idx < g0 + mcnt; ++idx) cp_async4(dst + ph + (idx - g0), src + idx);
+        }
+        if (expl) {
+          if (lane == 0 && sa1 > sa0)
+            bulk_g2s(SA + (size_t)(sph + sa0 - g0) * es, SID + (size_t)sa0 * es, (sa1 - sa0) * (uint32_t)es,
+                     &full[b]);
+          // ragged ends of the id column: fewer than 16 bytes each, plain loads
+          const uint32_t nlo = sa0 - g0, nhi = g0 + mcnt - sa1;
+          if ((uint32_t)lane < nlo + nhi) {
+            const uint32_t idx = (uint32_t)lane < nlo ? g0 + lane : sa1 + (lane - nlo);
+            if (es == 1)
+              SA[sph + idx - g0] = SID[idx];
+            else
+              ((uint16_t*)SA)[sph + idx - g0] = ((const uint16_t*)SID)[idx];
+          }
         }
         if (!P)
           for (uint32_t i = lane; i < mcnt; i += 32) A[(size_t)d * stride + i] = g0 + i;
@@ -188,47 +247,34 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       named_sync(kConsumerBar, kCT);
       if (s_fail) return;
       const SubMeta& m = meta[b];
-      const TreeDev& t = m.t;
-      const Cell& cell = m.cell;
-      const int level = cell.level;
-      const int d = t.d;
-      const int64_t n = t.n;
+      const int d = m.d;
+      const int64_t n = m.n;
       const uint32_t T = m.T, stride = T + 4, mcnt = m.mcnt, L = m.L;
-      const uint32_t tend = min(m.tile_start + (uint32_t)kTile, cell.count);
-      const int child_stall = (cell.count == L) ? cell.stall + 1 : 0;
-      const bool term_left = is_terminal(t, L, level + 1, child_stall);
-      const bool term_right = is_terminal(t, cell.count - L, level + 1, child_stall);
-      const bool want_mm = t.key_rule == KEY_WIDEST && !(term_left && term_right);
-      const bool explicit_sid = t.subset_mode == SUB_EXPLICIT;
-      const uint32_t g0 = cell.begin + m.sub;
+      const uint32_t cbeg = m.cell_begin, ccount = m.cell_count;
+      const uint32_t tend = min(m.tile_start + (uint32_t)kTile, ccount);
+      const bool term_left = m.term_left, term_right = m.term_right;
+      const bool want_mm = m.want_mm, want_off = m.want_off, level0 = m.level0;
+      const bool explicit_sid = m.sid_bytes != 0;
       if (m.sub == m.tile_start) {
-        lnext = cell.begin + m.loff;
-        rnext = cell.begin + L + (m.tile_start - m.loff);
+        lnext = cbeg + m.loff;
+        rnext = cbeg + L + (m.tile_start - m.loff);
         if (want_mm)
-          for (int j = lane; j < 2 * d * 2; j += 32) {
+          for (int j = tid; j < 4 * d; j += kCT) {
             const int side = j / (2 * d), l = (j / 2) % d, which = j & 1;
-            wmm[warp][side][l][which] = which ? 0u : 0xffffffffu;
+            tmm[side][l][which] = which ? 0u : 0xffffffffu;
           }
       }
-      uint32_t sidv[kMaxItems];
-      if (explicit_sid) {
-        const void* S = src_sid(t, level);
-#pragma unroll
-        for (int q = 0; q < kMaxItems; ++q) {
-          const uint32_t i = tid + q * kCT;
-          sidv[q] = 0;
-          if (i < mcnt)
-            sidv[q] = t.sid_bytes == 1 ? (uint32_t)((const uint8_t*)S)[g0 + i]
-                                       : (uint32_t)((const uint16_t*)S)[g0 + i];
-        }
-      }
       const uint32_t* A = sm + (size_t)b * (kBufBytes / 4);
+      const uint8_t* SA = (const uint8_t*)(A + (size_t)(d + 1) * stride) + (size_t)m.sid_ph * m.sid_bytes;
+      auto sid_of = [&](uint32_t i) -> uint32_t {
+        const uint32_t v = m.sid_bytes == 1 ? (uint32_t)SA[i] : (uint32_t)((const uint16_t*)SA)[i];
+        return min(v, m.r - 1u);
+      };
 
       // ---- flags and ranks (position order); subsets where offsets are kept
       bool left[kMaxItems];
       unsigned bal[kMaxItems];
       uint32_t sv[kMaxItems];
-      const bool want_off = m.row[0] != kNoRow || m.row[1] != kNoRow;
       const uint32_t* keycol = A + (size_t)m.dim * stride + m.ph[m.dim];
       const uint32_t* pa = A + (size_t)d * stride + m.ph[d];
 #pragma unroll
@@ -239,95 +285,116 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         if (lane == 0) wcnt[q][warp] = __popc(bal[q]);
         sv[q] = 0;
         if (want_off) {
-          if (i < mcnt) sv[q] = explicit_sid ? min(sidv[q], (uint32_t)t.r - 1u) : subset_from_orig(t, pa[i]);
+          if (i < mcnt) sv[q] = explicit_sid ? sid_of(i) : meta_subset(m, pa[i]);
           if (lane == 31) sedge[q][warp] = sv[q];
         }
       }
       named_sync(kConsumerBar, kCT);
+      // left points before each (round, warp) block: one scan over the
+      // kMaxItems * kCW = 32 block counts in position order
+      static_assert(kMaxItems * kCW == 32, "one lane per (round, warp) block");
+      const uint32_t wv = (&wcnt[0][0])[lane];
+      const uint32_t winc = warp_incl_scan(wv);
+      const uint32_t wexc = winc - wv;
+      const uint32_t nL = __shfl_sync(0xffffffffu, winc, 31);
       uint32_t dst[kMaxItems], lrk[kMaxItems];
-      uint32_t nL = 0;
+      bool keep[kMaxItems];  // the point's child is not terminal: its columns move
 #pragma unroll
       for (int q = 0; q < kMaxItems; ++q) {
-        uint32_t below = 0, round = 0;
-#pragma unroll
-        for (int w = 0; w < kCW; ++w) {
-          const uint32_t v = wcnt[q][w];
-          below += (w < warp) ? v : 0u;
-          round += v;
-        }
         const uint32_t i = tid + q * kCT;
-        const uint32_t lr = nL + below + __popc(bal[q] & lt_mask);
+        const uint32_t lr = __shfl_sync(0xffffffffu, wexc, q * kCW + warp) + __popc(bal[q] & lt_mask);
         dst[q] = left[q] ? lnext + lr : rnext + (i - lr);
-        lrk[q] = lnext - cell.begin + lr;  // points of the cell before this one that go left
-        nL += round;
+        lrk[q] = lnext - cbeg + lr;  // points of the cell before this one that go left
+        keep[q] = i < mcnt && !(left[q] ? term_left : term_right);
       }
 
-      // ---- stores, straight from shared memory
-      {
-        const uint32_t* a = A + (size_t)d * stride + m.ph[d];
-        uint32_t* Po = t.pbuf[level & 1];
+      // ---- permutation
 #pragma unroll
-        for (int q = 0; q < kMaxItems; ++q) {
-          const uint32_t i = tid + q * kCT;
-          if (i >= mcnt) continue;
-          if (left[q] ? term_left : term_right)
-            t.out_perm[dst[q]] = a[i];
-          else
-            Po[dst[q]] = a[i];
-        }
+      for (int q = 0; q < kMaxItems; ++q) {
+        const uint32_t i = tid + q * kCT;
+        if (i >= mcnt) continue;
+        if (keep[q])
+          m.pout[dst[q]] = pa[i];
+        else
+          m.out_perm[dst[q]] = pa[i];
       }
-      for (int c = 0; c < d; ++c) {
-        const uint32_t* a = A + (size_t)c * stride + m.ph[c];
-        float* out = t.xbuf[level & 1] + (int64_t)c * n;
-        uint32_t lmin = 0xffffffffu, lmax = 0u, rmin = 0xffffffffu, rmax = 0u;
+
+      // ---- coordinate columns, two at a time, straight from shared memory
+      for (int c = 0; c < d; c += 2) {
+        const bool two = c + 1 < d;
+        const uint32_t* a0 = A + (size_t)c * stride + m.ph[c];
+        const uint32_t* a1 = two ? A + (size_t)(c + 1) * stride + m.ph[c + 1] : a0;
+        float* o0 = m.xout + (int64_t)c * n;
+        float* o1 = m.xout + (int64_t)(c + 1) * n;
+        uint32_t v0[kMaxItems], v1[kMaxItems];
 #pragma unroll
         for (int q = 0; q < kMaxItems; ++q) {
           const uint32_t i = tid + q * kCT;
-          if (i >= mcnt) continue;
-          const uint32_t v = a[i];
-          if (level == 0) saw_nan |= is_nan_bits(__uint_as_float(v));
-          if (left[q] ? term_left : term_right) continue;
-          out[dst[q]] = __uint_as_float(v);
-          if (want_mm) {
-            const uint32_t key = ord_key(__uint_as_float(v));
-            if (left[q]) {
-              lmin = min(lmin, key);
-              lmax = max(lmax, key);
-            } else {
-              rmin = min(rmin, key);
-              rmax = max(rmax, key);
-            }
-          }
+          v0[q] = i < mcnt ? a0[i] : 0u;
+          v1[q] = i < mcnt ? a1[i] : 0u;
         }
+        if (level0)
+#pragma unroll
+          for (int q = 0; q < kMaxItems; ++q)
+            saw_nan |= (tid + q * kCT < mcnt) &&
+                       (is_nan_bits(__uint_as_float(v0[q])) || is_nan_bits(__uint_as_float(v1[q])));
+#pragma unroll
+        for (int q = 0; q < kMaxItems; ++q)
+          if (keep[q]) {
+            o0[dst[q]] = __uint_as_float(v0[q]);
+            if (two) o1[dst[q]] = __uint_as_float(v1[q]);
+          }
         if (want_mm) {
-          lmin = __reduce_min_sync(0xffffffffu, lmin);
-          lmax = __reduce_max_sync(0xffffffffu, lmax);
-          rmin = __reduce_min_sync(0xffffffffu, rmin);
-          rmax = __reduce_max_sync(0xffffffffu, rmax);
-          if (lane == 0) {
-            wmm[warp][0][c][0] = min(wmm[warp][0][c][0], lmin);
-            wmm[warp][0][c][1] = max(wmm[warp][0][c][1], lmax);
-            wmm[warp][1][c][0] = min(wmm[warp][1][c][0], rmin);
-            wmm[warp][1][c][1] = max(wmm[warp][1][c][1], rmax);
+          // min / max as floats (the widest rule only uses max - min, which -0
+          // and +0 do not change); keys are formed once per warp below
+          const float inf = __int_as_float(0x7f800000);
+          float mm[2][2][2] = {{{inf, -inf}, {inf, -inf}}, {{inf, -inf}, {inf, -inf}}};  // [col][side][min,max]
+#pragma unroll
+          for (int q = 0; q < kMaxItems; ++q)
+            if (keep[q]) {
+              const float x0 = __uint_as_float(v0[q]), x1 = __uint_as_float(v1[q]);
+              if (left[q]) {
+                mm[0][0][0] = fminf(mm[0][0][0], x0);
+                mm[0][0][1] = fmaxf(mm[0][0][1], x0);
+                mm[1][0][0] = fminf(mm[1][0][0], x1);
+                mm[1][0][1] = fmaxf(mm[1][0][1], x1);
+              } else {
+                mm[0][1][0] = fminf(mm[0][1][0], x0);
+                mm[0][1][1] = fmaxf(mm[0][1][1], x0);
+                mm[1][1][0] = fminf(mm[1][1][0], x1);
+                mm[1][1][1] = fmaxf(mm[1][1][1], x1);
+              }
+            }
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            if (cc == 1 && !two) break;
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+              const uint32_t lo = __reduce_min_sync(0xffffffffu, ord_key(mm[cc][side][0]));
+              const uint32_t hi = __reduce_max_sync(0xffffffffu, ord_key(mm[cc][side][1]));
+              if (lane == 0) {
+                atomic_min_shared(&tmm[side][c + cc][0], lo);
+                atomic_max_shared(&tmm[side][c + cc][1], hi);
+              }
+            }
           }
         }
       }
       if (explicit_sid) {
-        void* So = t.sbuf[level & 1];
 #pragma unroll
         for (int q = 0; q < kMaxItems; ++q) {
           const uint32_t i = tid + q * kCT;
-          if (i >= mcnt || (left[q] ? term_left : term_right)) continue;
-          if (t.sid_bytes == 1)
-            ((uint8_t*)So)[dst[q]] = (uint8_t)sidv[q];
+          if (!keep[q]) continue;
+          if (m.sid_bytes == 1)
+            ((uint8_t*)m.sout)[dst[q]] = SA[i];
           else
-            ((uint16_t*)So)[dst[q]] = (uint16_t)sidv[q];
+            ((uint16_t*)m.sout)[dst[q]] = ((const uint16_t*)SA)[i];
         }
       }
       // ---- subset offsets of the big children, at the segment starts
       // (each row holds r + 1 words below off_cap, checked when it was handed out)
       if (want_off) {
-        const uint32_t r = (uint32_t)t.r;
+        const uint32_t r = m.r;
 #pragma unroll
         for (int q = 0; q < kMaxItems; ++q) {
           const uint32_t i = tid + q * kCT;
@@ -341,10 +408,10 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
               if (m.row[0] != kNoRow) s.off_next[m.row[0] + u] = lrk[q];
               if (m.row[1] != kNoRow) s.off_next[m.row[1] + u] = p - lrk[q];
             }
-          if (p + 1 == cell.count)
+          if (p + 1 == ccount)
             for (uint32_t u = sv[q] + 1; u <= r; ++u) {
               if (m.row[0] != kNoRow) s.off_next[m.row[0] + u] = L;
-              if (m.row[1] != kNoRow) s.off_next[m.row[1] + u] = cell.count - L;
+              if (m.row[1] != kNoRow) s.off_next[m.row[1] + u] = ccount - L;
             }
         }
       }
@@ -352,18 +419,13 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       rnext += mcnt - nL;
       more = m.sub + T < tend;
       if (!more) {  // last sub-tile of the tile
-        if (saw_nan) set_status(t, ST_NAN_INPUT);
+        if (saw_nan) atomicCAS(m.status, ST_OK, ST_NAN_INPUT);
         saw_nan = false;
         if (want_mm) {
           named_sync(kConsumerBar, kCT);
-          for (int j = tid; j < 2 * d * 2; j += kCT) {
+          for (int j = tid; j < 4 * d; j += kCT) {
             const int side = j / (2 * d), l = (j / 2) % d, which = j & 1;
-            uint32_t v = wmm[0][side][l][which];
-            for (int w = 1; w < kCW; ++w) {
-              const uint32_t u = wmm[w][side][l][which];
-              v = which ? max(v, u) : min(v, u);
-            }
-            s.tile_mm[(((size_t)m.tile * 2 + side) * kMaxDims + l) * 2 + which] = v;
+            s.tile_mm[(((size_t)m.tile * 2 + side) * kMaxDims + l) * 2 + which] = tmm[side][l][which];
           }
         }
       }

@@ -3,17 +3,23 @@
 //
 // A cell with at most subtree_capacity(d) points is staged once into shared
 // memory with bulk asynchronous copies (cp.async.bulk, completion on an
-// mbarrier): all d coordinate columns and the permutation. Then, level by
-// level (paper, Sec. 2: each level splits every cell of the previous one
-// along its key), for all live local cells at once:
+// mbarrier): all d coordinate columns and the permutation. Its points are in
+// subset order (the layout invariant of kdt_internal.cuh; the root of a small
+// tree is put in that order here by a counting sort), and the local order is
+// kept by stable partitions, so every (cell, subset) segment is a contiguous
+// run of positions. Then, level by level (paper, Sec. 2: each level splits
+// every cell of the previous one along its key), for all live local cells at
+// once:
 //   1. key coordinate (cyclic, or widest range);
-//   2. counting sort of the points by (cell, subset) into bins, in batches of
-//      at most kSubtreeBins bins, gathering each bin's keys contiguously; the
-//      lower median of every bin by per-point rank counting (bins of at most
-//      kRankMax points) or a warp radix select (larger bins);
-//   3. per cell, the count-weighted lower median of its bins' medians;
-//   4. a stable partition of the local order around the split (ties left);
-//   5. children: terminal cells are recorded, the others form the next level.
+//   2. the key of every position on its cell's coordinate, and the segment
+//      starts (a cell's first position, or a change of subset), numbered by
+//      one block-wide scan;
+//   3. the lower median of every segment: rank counting inside the segment
+//      (at most kRankMax points), else a warp radix select over the bits
+//      where its keys differ;
+//   4. per cell, the count-weighted lower median of its segments' medians;
+//   5. a stable partition of the local order around the split (ties left);
+//   6. children: terminal cells are recorded, the others form the next level.
 // The permutation is written once, at the end. The kernel is persistent: each
 // CTA pulls cells from a queue.
 #include <algorithm>
@@ -30,24 +36,24 @@ namespace {
 constexpr int T = kSubtreeThreads;
 constexpr int NW = kSubtreeWarps;
 constexpr uint16_t kNoCell = 0xffff;
-constexpr uint32_t kRankMax = 24;
+constexpr uint32_t kRankMax = 32;
 
 // -------------------------------------------------------- shared layout
 
 struct Smem {
-  uint32_t* bins;     // kSubtreeBins + 1 (also the widest min/max table)
-  uint32_t* med;      // kSubtreeBins
-  uint32_t* whist;    // NW * 256
-  uint16_t* biglist;  // kSubtreeBigBinCap
+  uint32_t* whist;    // NW * 256 words: warp histograms, tables of few cells, root subset counts
+  uint16_t* biglist;  // kSubtreeBigCap segments above kRankMax points
   LCell* tab[2];      // kSubtreeSmemCells each
-  uint32_t* keys;     // (d + 1) columns at stride `stride`; column d is the permutation
-  uint32_t* gk;       // N: keys gathered in bin order
-  uint16_t* sid;      // N
-  uint16_t* ordA;     // N
+  uint32_t* cols;     // (d + 1) columns at stride `stride`; column d is the permutation
+  uint32_t* gk;       // N: key of each position on its cell's coordinate
+  uint32_t* smed;     // N: median of each segment
+  uint16_t* sid;      // N: subset of each local point
+  uint16_t* ordA;     // N: local point at each position
   uint16_t* ordB;     // N
-  uint16_t* cellid;   // N
-  uint16_t* pre;      // N + 1
-  uint16_t* aux;      // N: bin of a gathered position, then the left flag of a position
+  uint16_t* cellid;   // N: live cell of each position (kNoCell: finished)
+  uint16_t* pre;      // N + 1: exclusive prefix of `aux`
+  uint16_t* segs;     // N + 1: first position of each segment
+  uint16_t* aux;      // N: segment-start flag, then left flag
 };
 
 __device__ __forceinline__ uint8_t* al16(uint8_t* p) {
@@ -57,58 +63,75 @@ __device__ __forceinline__ uint8_t* al16(uint8_t* p) {
 __device__ Smem carve(uint8_t* base, uint32_t N, int d) {
   Smem s;
   uint8_t* p = base;
-  s.bins = (uint32_t*)p;
-  p += 16400;
-  s.med = (uint32_t*)p;
-  p += kSubtreeBins * 4;
   s.whist = (uint32_t*)p;
-  p += NW * 256 * 4;
+  p += (size_t)NW * 256 * 4;
   s.biglist = (uint16_t*)p;
-  p += kSubtreeBigBinCap * 2;
+  p += kSubtreeBigCap * 2;
   s.tab[0] = (LCell*)p;
   p += kSubtreeSmemCells * sizeof(LCell);
   s.tab[1] = (LCell*)p;
   p += kSubtreeSmemCells * sizeof(LCell);
   const uint32_t stride = subtree_stride(N);
-  s.keys = (uint32_t*)p;
+  s.cols = (uint32_t*)p;
   p += (size_t)(d + 1) * stride * 4;
   s.gk = (uint32_t*)p;
   p = al16(p + (size_t)N * 4);
-  uint16_t** arr[6] = {&s.sid, &s.ordA, &s.ordB, &s.cellid, &s.pre, &s.aux};
-  for (int i = 0; i < 6; ++i) {
+  s.smed = (uint32_t*)p;
+  p = al16(p + (size_t)N * 4);
+  uint16_t** arr[7] = {&s.sid, &s.ordA, &s.ordB, &s.cellid, &s.pre, &s.segs, &s.aux};
+  for (int i = 0; i < 7; ++i) {
     *arr[i] = (uint16_t*)p;
     p = al16(p + ((size_t)N + 1) * 2);
   }
   return s;
 }
 
-// Radix select over a contiguous run of keys in shared memory (one warp).
-__device__ uint32_t warp_select_smem(const uint32_t* keys, uint32_t w, uint32_t rank, uint32_t* hist) {
-  const int lane = threadIdx.x & 31;
-  uint32_t prefix = 0, mask = 0;
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int i = lane; i < 256; i += 32) hist[i] = 0;
-    __syncwarp();
-    for (uint32_t i = lane; i < w; i += 32) {
-      const uint32_t k = keys[i];
-      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
-    }
-    __syncwarp();
-    uint32_t below;
-    const uint32_t digit = warp_find_digit(hist, rank, &below);
-    rank -= below;
-    prefix |= digit << shift;
-    mask |= 255u << shift;
-    __syncwarp();
-  }
-  return prefix;
-}
-
 __device__ __forceinline__ double key_range(uint32_t lo, uint32_t hi) {
   return (lo == hi) ? 0.0 : (double)key_float(hi) - (double)key_float(lo);
 }
 
-__global__ void __launch_bounds__(T, 1)
+// Widest coordinate of one cell from its per-coordinate min and max keys
+// (coordinate l in lane l % 32, slot l / 32): the largest range
+// (double)max - (double)min, 0 for equal keys, lowest coordinate on ties.
+__device__ __forceinline__ int warp_pick_widest(const uint32_t (&lo)[2], const uint32_t (&hi)[2], int d) {
+  const int lane = threadIdx.x & 31;
+  const double r0 = lane < d ? key_range(lo[0], hi[0]) : -1.0;
+  const double r1 = lane + 32 < d ? key_range(lo[1], hi[1]) : -1.0;
+  double rb = r0;
+  int ib = lane;
+  if (r1 > r0) {
+    rb = r1;
+    ib = lane + 32;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double orb = __shfl_xor_sync(0xffffffffu, rb, o);
+    const int oib = __shfl_xor_sync(0xffffffffu, ib, o);
+    if (orb > rb || (orb == rb && oib < ib)) {
+      rb = orb;
+      ib = oib;
+    }
+  }
+  return ib;
+}
+
+// Block-wide exclusive scan of the flags f[0..N) into pre[0..N], pre[N] the
+// total; each thread scans a run of consecutive positions.
+__device__ __forceinline__ void scan_flags(const uint16_t* f, uint16_t* pre, uint32_t N, uint32_t* tmp) {
+  const uint32_t per = (N + T - 1) / T;
+  const uint32_t i0 = min(N, threadIdx.x * per), i1 = min(N, i0 + per);
+  uint32_t sum = 0;
+  for (uint32_t i = i0; i < i1; ++i) sum += f[i];
+  uint32_t tot;
+  uint32_t run = block_excl_scan(sum, tmp, &tot);
+  for (uint32_t i = i0; i < i1; ++i) {
+    pre[i] = (uint16_t)run;
+    run += f[i];
+  }
+  if (threadIdx.x == 0) pre[N] = (uint16_t)tot;
+}
+
+__global__ void __launch_bounds__(T, kSubtreeCtasPerSm)
 k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head, LCell* slices,
           uint32_t slice_cells) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -116,6 +139,10 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
   __shared__ uint32_t s_item, s_ncur, s_nbig, s_where, s_fail;
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_colbase[kMaxDims + 1];
+  struct CombineState {
+    uint32_t lo, hi, rem, prefix, rank;
+  };
+  __shared__ CombineState s_cmb[kSubtreeWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   LCell* gslice[2] = {slices + (size_t)blockIdx.x * 2 * slice_cells,
                       slices + (size_t)blockIdx.x * 2 * slice_cells + slice_cells};
@@ -140,7 +167,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
     const int64_t n = t.n;
     const uint32_t stride = subtree_stride(N);
     Smem S = carve(smem_raw, N, d);
-    // Column l of the cell sits at S.keys + s_colbase[l]; column d holds the
+    // Column l of the cell sits at S.cols + s_colbase[l]; column d holds the
     // permutation. Each column's offset absorbs the 16-byte alignment phase
     // of its global source so that the bulk copies are aligned on both sides.
 
@@ -172,7 +199,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
           const uint32_t a0 = min(b0 + ((4u - ph) & 3u), e0);
           const uint32_t a1 = a0 + ((e0 - a0) & ~3u);
           if (a1 > a0)
-            bulk_g2s(S.keys + (size_t)l * stride + ph + (a0 - b0), src_of(l) + a0, (a1 - a0) * 4u, &s_bar);
+            bulk_g2s(S.cols + (size_t)l * stride + ph + (a0 - b0), src_of(l) + a0, (a1 - a0) * 4u, &s_bar);
         }
       }
       for (int j = tid; j < ncols * 8; j += T) {
@@ -182,10 +209,10 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
         const uint32_t a1 = a0 + ((e0 - a0) & ~3u);
         const uint32_t idx = e < 4 ? b0 + e : a1 + (e - 4);
         const bool ok = e < 4 ? (idx < a0) : (idx < e0);
-        if (ok) S.keys[(size_t)l * stride + ph + (idx - b0)] = src_of(l)[idx];
+        if (ok) S.cols[(size_t)l * stride + ph + (idx - b0)] = src_of(l)[idx];
       }
       __syncthreads();
-      uint32_t* pm0 = S.keys + s_colbase[d];
+      uint32_t* pm0 = S.cols + s_colbase[d];
       if (!P)
         for (uint32_t i = tid; i < N; i += T) pm0[i] = b0 + i;
       if (!mbar_wait_bounded(&s_bar, phase)) {
@@ -200,7 +227,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
       }
       bool nan = false;
       for (int l = 0; l < d; ++l) {
-        uint32_t* col = S.keys + s_colbase[l];
+        uint32_t* col = S.cols + s_colbase[l];
         for (uint32_t i = tid; i < N; i += T) {
           const float x = __uint_as_float(col[i]);
           nan |= is_nan_bits(x);
@@ -211,8 +238,30 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
       const void* SID = src_sid(t, c.level);
       for (uint32_t i = tid; i < N; i += T) {
         S.sid[i] = (uint16_t)subset_of(t, SID, pm0[i], (int64_t)b0 + i);
-        S.ordA[i] = (uint16_t)i;
         S.cellid[i] = 0;
+      }
+      // The root of a small tree arrives in index order: put it in subset
+      // order (counting sort; order inside a subset is immaterial). Every
+      // other cell is in subset order already.
+      const bool sort_root = c.level == 0 && t.subset_mode != SUB_CONTIG && r > 1;
+      if (sort_root) {
+        for (int j = tid; j < r; j += T) S.whist[j] = 0;
+        __syncthreads();
+        for (uint32_t i = tid; i < N; i += T) S.ordB[i] = (uint16_t)atomic_add_shared(&S.whist[S.sid[i]], 1u);
+        __syncthreads();
+        uint32_t run = 0;
+        for (int j0 = 0; j0 < r; j0 += T) {
+          const int j = j0 + tid;
+          const uint32_t v = j < r ? S.whist[j] : 0u;
+          uint32_t tot;
+          const uint32_t ex = block_excl_scan(v, tmp, &tot);
+          if (j < r) S.whist[j] = run + ex;
+          run += tot;
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < N; i += T) S.ordA[S.whist[S.sid[i]] + S.ordB[i]] = (uint16_t)i;
+      } else {
+        for (uint32_t i = tid; i < N; i += T) S.ordA[i] = (uint16_t)i;
       }
       if (tid == 0) {
         S.tab[0][0] = LCell{c.heap, 0u, 0, (uint16_t)N, 0, 0, (uint8_t)c.stall};
@@ -222,7 +271,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
     }
     __syncthreads();
 
-    const uint32_t* pm = S.keys + s_colbase[d];
+    const uint32_t* pm = S.cols + s_colbase[d];
     uint16_t* ordA = S.ordA;
     uint16_t* ordB = S.ordB;
     int which = 0;
@@ -235,228 +284,284 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
       // ---- 1. key coordinate of every live cell
       if (t.key_rule == KEY_CYCLIC) {
         for (uint32_t k = tid; k < ncur; k += T) cc[k].dim = (uint8_t)(level % d);
-      } else if (ncur >= (uint32_t)NW) {
-        for (uint32_t k = warp; k < ncur; k += NW) {
-          const uint32_t b = cc[k].begin, e = b + cc[k].count;
-          int best = 0;
-          double best_range = -1.0;
-          for (int l = 0; l < d; ++l) {
-            const uint32_t* col = S.keys + s_colbase[l];
-            uint32_t lo = 0xffffffffu, hi = 0u;
-            for (uint32_t i = b + lane; i < e; i += 32) {
-              const uint32_t kk = col[ordA[i]];
-              lo = min(lo, kk);
-              hi = max(hi, kk);
-            }
-            lo = warp_min(lo);
-            hi = warp_max(hi);
-            const double range = key_range(lo, hi);
-            if (range > best_range) {
-              best_range = range;
-              best = l;
-            }
-          }
-          if (lane == 0) cc[k].dim = (uint8_t)best;
-        }
       } else {
-        uint32_t* tab = S.bins;  // [ncur][d][2]
-        for (uint32_t j = tid; j < ncur * (uint32_t)d; j += T) {
-          tab[2 * j] = 0xffffffffu;
-          tab[2 * j + 1] = 0u;
+        // per (cell, part): min and max key of every coordinate, coordinate l
+        // ending in lane l % 32; G warps share a cell when there are few cells
+        const uint32_t G = ncur >= (uint32_t)NW ? 1u : (uint32_t)NW / ncur;
+        uint32_t* tab = S.whist;  // few cells: [ncur][d][2]
+        if (G > 1) {
+          for (uint32_t j = tid; j < ncur * (uint32_t)d; j += T) {
+            tab[2 * j] = 0xffffffffu;
+            tab[2 * j + 1] = 0u;
+          }
+          __syncthreads();
         }
-        __syncthreads();
-        const uint32_t G = NW / ncur;
-        const uint32_t k = warp / G, part = warp % G;
-        if (k < ncur) {
+        for (uint32_t w0 = warp; w0 < ncur * G; w0 += NW) {
+          const uint32_t k = w0 / G, part = w0 % G;
           const uint32_t b = cc[k].begin, cnt = cc[k].count;
           const uint32_t i0 = b + (cnt * part) / G, i1 = b + (cnt * (part + 1)) / G;
-          for (int l = 0; l < d; ++l) {
-            const uint32_t* col = S.keys + s_colbase[l];
-            uint32_t lo = 0xffffffffu, hi = 0u;
+          uint32_t lo2[2] = {0xffffffffu, 0xffffffffu}, hi2[2] = {0u, 0u};
+          for (int c0 = 0; c0 < d; c0 += 8) {
+            const int nc = min(8, d - c0);
+            uint32_t base[8], lo[8], hi[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              base[q] = q < nc ? s_colbase[c0 + q] : 0u;
+              lo[q] = 0xffffffffu;
+              hi[q] = 0u;
+            }
             for (uint32_t i = i0 + lane; i < i1; i += 32) {
-              const uint32_t kk = col[ordA[i]];
-              lo = min(lo, kk);
-              hi = max(hi, kk);
+              const uint32_t o = ordA[i];
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                if (q < nc) {
+                  const uint32_t kk = S.cols[base[q] + o];
+                  lo[q] = min(lo[q], kk);
+                  hi[q] = max(hi[q], kk);
+                }
             }
-            lo = warp_min(lo);
-            hi = warp_max(hi);
-            if (lane == 0) {
-              atomicMin(&tab[(k * d + l) * 2], lo);
-              atomicMax(&tab[(k * d + l) * 2 + 1], hi);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              if (q < nc) {
+                const uint32_t l = __reduce_min_sync(0xffffffffu, lo[q]);
+                const uint32_t h = __reduce_max_sync(0xffffffffu, hi[q]);
+                const int col = c0 + q;
+                if (lane == (col & 31)) {
+                  lo2[col >> 5] = l;
+                  hi2[col >> 5] = h;
+                }
+              }
+          }
+          if (G == 1) {
+            const int best = warp_pick_widest(lo2, hi2, d);
+            if (lane == 0) cc[k].dim = (uint8_t)best;
+          } else {
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int col = lane + 32 * h2;
+              if (col < d) {
+                atomic_min_shared(&tab[(k * d + col) * 2], lo2[h2]);
+                atomic_max_shared(&tab[(k * d + col) * 2 + 1], hi2[h2]);
+              }
             }
           }
         }
-        __syncthreads();
-        for (uint32_t kk = tid; kk < ncur; kk += T) {
-          int best = 0;
-          double best_range = -1.0;
-          for (int l = 0; l < d; ++l) {
-            const double range = key_range(tab[(kk * d + l) * 2], tab[(kk * d + l) * 2 + 1]);
-            if (range > best_range) {
-              best_range = range;
-              best = l;
+        if (G > 1) {
+          __syncthreads();
+          for (uint32_t k = warp; k < ncur; k += NW) {
+            uint32_t lo2[2], hi2[2];
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int col = lane + 32 * h2;
+              lo2[h2] = col < d ? tab[(k * d + col) * 2] : 0u;
+              hi2[h2] = col < d ? tab[(k * d + col) * 2 + 1] : 0u;
             }
+            const int best = warp_pick_widest(lo2, hi2, d);
+            if (lane == 0) cc[k].dim = (uint8_t)best;
           }
-          cc[kk].dim = (uint8_t)best;
         }
       }
       __syncthreads();
 
-      // ---- 2/3. per-(cell, subset) medians and their weighted median, in batches
-      const uint32_t CB = max(1u, (uint32_t)kSubtreeBins / (uint32_t)r);
-      for (uint32_t kb0 = 0; kb0 < ncur; kb0 += CB) {
-        const uint32_t ke = min(ncur, kb0 + CB);
-        const uint32_t nb = (ke - kb0) * (uint32_t)r;
-        const uint32_t pb = cc[kb0].begin;
-        const uint32_t pe = cc[ke - 1].begin + cc[ke - 1].count;
-        for (uint32_t b = tid; b <= nb; b += T) S.bins[b] = 0;
-        if (tid == 0) s_nbig = 0;
-        __syncthreads();
-        for (uint32_t i = pb + tid; i < pe; i += T) {
-          const uint16_t k = S.cellid[i];
-          if (k == kNoCell) continue;
-          const uint32_t b = (k - kb0) * (uint32_t)r + S.sid[ordA[i]];
-          S.pre[i] = (uint16_t)atomicAdd(&S.bins[b], 1u);
+      // ---- 2. keys in local order, segment starts, their numbering
+      for (uint32_t i = tid; i < N; i += T) {
+        const uint16_t k = S.cellid[i];
+        uint16_t f = 0;
+        if (k != kNoCell) {
+          const uint32_t o = ordA[i];
+          S.gk[i] = S.cols[s_colbase[cc[k].dim] + o];
+          f = (i == cc[k].begin) || S.sid[o] != S.sid[ordA[i - 1]];
         }
-        __syncthreads();
-        {  // exclusive scan of bins[0..nb), total in bins[nb]
-          const uint32_t per = (nb + T - 1) / T;
-          const uint32_t q0 = min(nb, tid * per), q1 = min(nb, q0 + per);
-          uint32_t sum = 0;
-          for (uint32_t b = q0; b < q1; ++b) sum += S.bins[b];
-          uint32_t tot;
-          uint32_t run = block_excl_scan(sum, tmp, &tot);
-          for (uint32_t b = q0; b < q1; ++b) {
-            const uint32_t v = S.bins[b];
-            S.bins[b] = run;
-            run += v;
+        S.aux[i] = f;
+      }
+      if (tid == 0) s_nbig = 0;
+      __syncthreads();
+      scan_flags(S.aux, S.pre, N, tmp);
+      __syncthreads();
+      const uint32_t nseg = S.pre[N];
+      for (uint32_t i = tid; i < N; i += T)
+        if (S.aux[i]) S.segs[S.pre[i]] = (uint16_t)i;
+      if (tid == 0) S.segs[nseg] = (uint16_t)N;
+      __syncthreads();
+
+      // ---- 3. lower median of every segment
+      for (uint32_t i = tid; i < N; i += T) {
+        const uint16_t k = S.cellid[i];
+        if (k == kNoCell) continue;
+        const uint32_t sx = (uint32_t)S.pre[i] + S.aux[i] - 1u;
+        const uint32_t b = S.segs[sx], e = min((uint32_t)S.segs[sx + 1], (uint32_t)cc[k].begin + cc[k].count);
+        const uint32_t w = e - b;
+        if (w > kRankMax) {
+          if (i == b) {
+            const uint32_t slot = atomicAdd(&s_nbig, 1u);
+            if (slot < (uint32_t)kSubtreeBigCap) S.biglist[slot] = (uint16_t)sx; else set_status(t, ST_INTERNAL);
           }
-          if (tid == 0) S.bins[nb] = tot;
+          continue;
         }
-        __syncthreads();
-        const uint32_t nact = S.bins[nb];
-        for (uint32_t i = pb + tid; i < pe; i += T) {
-          const uint16_t k = S.cellid[i];
-          if (k == kNoCell) continue;
-          const uint32_t b = (k - kb0) * (uint32_t)r + S.sid[ordA[i]];
-          const uint32_t pos = pb + S.bins[b] + S.pre[i];
-          ordB[pos] = ordA[i];
-          S.aux[pos] = (uint16_t)b;
-          S.gk[pos] = S.keys[s_colbase[cc[k].dim] + ordA[i]];
+        const uint32_t key = S.gk[i];
+        uint32_t rk = 0;
+        for (uint32_t j = b; j < e; ++j) {
+          const uint32_t kj = S.gk[j];
+          rk += (kj < key) | ((kj == key) & (j < i));
         }
-        __syncthreads();
-        for (uint32_t q = pb + tid; q < pb + nact; q += T) {
-          const uint32_t b = S.aux[q];
-          const uint32_t bs = pb + S.bins[b], be = pb + S.bins[b + 1];
-          const uint32_t w = be - bs;
-          if (w > kRankMax) {
-            if (q == bs) S.biglist[atomicAdd(&s_nbig, 1u)] = (uint16_t)b;
-            continue;
-          }
-          const uint32_t k = S.gk[q];
-          uint32_t rk = 0;
-          for (uint32_t j = bs; j < be; ++j) {
-            const uint32_t kj = S.gk[j];
-            rk += (kj < k) | ((kj == k) & (j < q));
-          }
-          if (rk == (w - 1) / 2) S.med[b] = k;
-        }
-        __syncthreads();
-        const uint32_t nbig = s_nbig;
+        if (rk == (w - 1) / 2) S.smed[sx] = key;
+      }
+      __syncthreads();
+      {
+        const uint32_t nbig = min(s_nbig, (uint32_t)kSubtreeBigCap);
         for (uint32_t j = warp; j < nbig; j += NW) {
-          const uint32_t b = S.biglist[j];
-          const uint32_t bs = pb + S.bins[b], w = S.bins[b + 1] - S.bins[b];
-          const uint32_t m = warp_select_smem(S.gk + bs, w, (w - 1) / 2, S.whist + warp * 256);
-          if (lane == 0) S.med[b] = m;
-        }
-        __syncthreads();
-        // weighted lower median per cell: smallest bin median m whose bins with
-        // median <= m hold >= ceil(W/2) points (weighted 8-bit radix select)
-        const uint32_t ncb = ke - kb0;
-        if (ncb >= (uint32_t)NW) {
-          for (uint32_t k = kb0 + warp; k < ke; k += NW) {
-            uint32_t* hist = S.whist + warp * 256;
-            const uint32_t q0 = (k - kb0) * (uint32_t)r;
-            uint32_t rank = (cc[k].count - 1u) / 2u, prefix = 0, mask = 0;
-            for (int shift = 24; shift >= 0; shift -= 8) {
-              for (int i = lane; i < 256; i += 32) hist[i] = 0;
-              __syncwarp();
-              for (int j = lane; j < r; j += 32) {
-                const uint32_t w = S.bins[q0 + j + 1] - S.bins[q0 + j];
-                const uint32_t key = S.med[q0 + j];
-                if (w && (key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], w);
-              }
-              __syncwarp();
-              uint32_t below;
-              const uint32_t digit = warp_find_digit(hist, rank, &below);
-              rank -= below;
-              prefix |= digit << shift;
-              mask |= 255u << shift;
-              __syncwarp();
-            }
-            if (lane == 0) cc[k].mkey = prefix;
-          }
-        } else {
-          // few cells: G warps per cell share one histogram per cell
-          const uint32_t G = NW / ncb;
-          const uint32_t kk = warp / G, part = warp % G;
-          uint32_t* hist = S.whist + (kk < ncb ? kk : 0) * 256;
-          uint32_t rank = kk < ncb ? (cc[kb0 + kk].count - 1u) / 2u : 0u, prefix = 0, mask = 0;
-          const uint32_t q0 = kk * (uint32_t)r;
-          for (int shift = 24; shift >= 0; shift -= 8) {
-            for (uint32_t i = tid; i < ncb * 256u; i += T) S.whist[i] = 0;
-            __syncthreads();
-            if (kk < ncb) {
-              for (uint32_t j = part * 32 + lane; j < (uint32_t)r; j += G * 32) {
-                const uint32_t w = S.bins[q0 + j + 1] - S.bins[q0 + j];
-                const uint32_t key = S.med[q0 + j];
-                if (w && (key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], w);
-              }
-            }
-            __syncthreads();
-            if (kk < ncb) {
-              uint32_t below;
-              const uint32_t digit = warp_find_digit(hist, rank, &below);
-              rank -= below;
-              prefix |= digit << shift;
-              mask |= 255u << shift;
-            }
-            __syncthreads();
-          }
-          if (kk < ncb && part == 0 && lane == 0) cc[kb0 + kk].mkey = prefix;
-        }
-        __syncthreads();
-        for (uint32_t k = kb0 + tid; k < ke; k += T) {
-          t.out_vals[cc[k].heap] = key_float(cc[k].mkey);
-          t.out_dims[cc[k].heap] = (int8_t)cc[k].dim;
+          const uint32_t sx = S.biglist[j];
+          const uint32_t b = S.segs[sx];
+          const uint16_t k = S.cellid[b];
+          const uint32_t e = min((uint32_t)S.segs[sx + 1], (uint32_t)cc[k].begin + cc[k].count);
+          const uint32_t* g = S.gk + b;
+          const uint32_t m = warp_weighted_select<true>(e - b, (e - b - 1) / 2, S.whist + warp * 256,
+                                                        [&](uint32_t jj) { return g[jj]; },
+                                                        [](uint32_t) { return 1u; });
+          if (lane == 0) S.smed[sx] = m;
         }
       }
       __syncthreads();
 
-      // ---- 4. stable partition of the local order (key <= split to the left)
+      // ---- 4. weighted lower median per cell: the smallest segment median m
+      // whose segments with median <= m hold >= ceil(W/2) points, i.e. the
+      // key of weighted rank (W-1)/2. A cell's segments are [pre[begin], pre[end]).
+      if (ncur >= (uint32_t)NW) {  // many cells: a warp per cell
+        for (uint32_t k = warp; k < ncur; k += NW) {
+          const uint32_t b = cc[k].begin, e = b + cc[k].count;
+          const uint32_t s0 = S.pre[b], s1 = S.pre[e];
+          const uint32_t m = warp_weighted_select(
+              s1 - s0, (cc[k].count - 1u) / 2u, S.whist + warp * 256, [&](uint32_t j) { return S.smed[s0 + j]; },
+              [&](uint32_t j) { return min((uint32_t)S.segs[s0 + j + 1], e) - S.segs[s0 + j]; });
+          if (lane == 0) cc[k].mkey = m;
+        }
+      } else {
+        // few cells: G warps per cell, each counting into its own histogram;
+        // the finder of a cell sums its G histograms. Every cell starts at the
+        // first bit where its segment medians differ.
+        const uint32_t G = (uint32_t)NW / ncur;
+        const uint32_t k = warp / G, part = warp % G;
+        uint32_t e = 0, s0 = 0, s1 = 0;
+        if (k < ncur) {
+          const uint32_t b = cc[k].begin;
+          e = b + cc[k].count;
+          s0 = S.pre[b];
+          s1 = S.pre[e];
+        }
+        if (tid < ncur) {
+          s_cmb[tid].lo = 0xffffffffu;
+          s_cmb[tid].hi = 0u;
+        }
+        __syncthreads();
+        if (k < ncur) {
+          uint32_t lo = 0xffffffffu, hi = 0u;
+          for (uint32_t j = s0 + part * 32 + lane; j < s1; j += G * 32) {
+            lo = min(lo, S.smed[j]);
+            hi = max(hi, S.smed[j]);
+          }
+          lo = __reduce_min_sync(0xffffffffu, lo);
+          hi = __reduce_max_sync(0xffffffffu, hi);
+          if (lane == 0) {
+            atomic_min_shared(&s_cmb[k].lo, lo);
+            atomic_max_shared(&s_cmb[k].hi, hi);
+          }
+        }
+        __syncthreads();
+        if (tid < ncur) {
+          const uint32_t lo = s_cmb[tid].lo, hi = s_cmb[tid].hi;
+          const int rem = lo >= hi ? 0 : 32 - __clz(lo ^ hi);
+          s_cmb[tid].rem = (uint32_t)rem;
+          s_cmb[tid].prefix = rem == 0 ? lo : (rem == 32 ? 0u : (lo & ~((1u << rem) - 1u)));
+          s_cmb[tid].rank = (cc[tid].count - 1u) / 2u;
+        }
+        __syncthreads();
+        for (;;) {
+          uint32_t more = 0;
+          for (uint32_t kk = 0; kk < ncur; ++kk) more |= s_cmb[kk].rem;
+          if (!more) break;
+          uint32_t rem = 0, prefix = 0, shift = 0, nb = 1, hmask = 0;
+          if (k < ncur) {
+            rem = s_cmb[k].rem;
+            prefix = s_cmb[k].prefix;
+            const uint32_t bits = rem < 8u ? rem : 8u;
+            shift = rem - bits;
+            nb = 1u << bits;
+            hmask = rem >= 32u ? 0u : ~((1u << rem) - 1u);
+          }
+          uint32_t* hist = S.whist + warp * 256;
+          for (uint32_t i = lane; i < 256u; i += 32) hist[i] = 0;
+          __syncwarp();
+          if (k < ncur && rem > 0)
+            for (uint32_t j = s0 + part * 32 + lane; j < s1; j += G * 32) {
+              const uint32_t key = S.smed[j];
+              if ((key & hmask) == prefix)
+                atomic_add_shared(&hist[(key >> shift) & (nb - 1u)], min((uint32_t)S.segs[j + 1], e) - S.segs[j]);
+            }
+          __syncthreads();
+          if (k < ncur && part == 0 && rem > 0) {
+            // sum the cell's G histograms while finding the digit
+            const uint32_t per = nb >= 32u ? nb / 32u : 1u;
+            const uint32_t first = lane * per;
+            uint32_t local[8];
+            uint32_t sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              uint32_t v = 0;
+              if ((uint32_t)q < per && first + q < nb)
+                for (uint32_t g = 0; g < G; ++g) v += hist[g * 256u + first + q];
+              local[q] = v;
+              sum += v;
+            }
+            const uint32_t rank = s_cmb[k].rank;
+            const uint32_t incl = warp_incl_scan(sum), excl = incl - sum;
+            const unsigned bal = __ballot_sync(0xffffffffu, rank >= excl && rank < incl);
+            const int owner = bal ? __ffs(bal) - 1 : 31;
+            if (lane == owner) {
+              uint32_t acc = excl, digit = 0;
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                if ((uint32_t)q < per && rank < acc + local[q]) {
+                  digit = first + q;
+                  break;
+                }
+                acc += local[q];
+              }
+              s_cmb[k].rank = rank - acc;
+              s_cmb[k].prefix = prefix | (digit << shift);
+              s_cmb[k].rem = shift;
+            }
+          }
+          __syncthreads();
+        }
+        if (tid < ncur) cc[tid].mkey = s_cmb[tid].prefix;
+      }
+      __syncthreads();
+      for (uint32_t k = tid; k < ncur; k += T) {
+        t.out_vals[cc[k].heap] = key_float(cc[k].mkey);
+        t.out_dims[cc[k].heap] = (int8_t)cc[k].dim;
+      }
+
+      // ---- 5. stable partition of the local order (key <= split to the left);
+      // the left flags are formed inside the scan
       {
         const uint32_t per = (N + T - 1) / T;
-        const uint32_t i0 = min(N, tid * per), i1 = min(N, i0 + per);
+        const uint32_t q0 = min(N, tid * per), q1 = min(N, q0 + per);
         uint32_t sum = 0;
-        for (uint32_t i = i0; i < i1; ++i) {
-          const uint16_t k = S.cellid[i];
-          uint16_t f = 0;
-          if (k != kNoCell) f = S.keys[s_colbase[cc[k].dim] + ordA[i]] <= cc[k].mkey;
-          S.aux[i] = f;
+        for (uint32_t q = q0; q < q1; ++q) {
+          const uint16_t k = S.cellid[q];
+          const uint16_t f = (k != kNoCell) && S.gk[q] <= cc[k].mkey;
+          S.aux[q] = f;
           sum += f;
         }
         uint32_t tot;
         uint32_t run = block_excl_scan(sum, tmp, &tot);
-        for (uint32_t i = i0; i < i1; ++i) {
-          S.pre[i] = (uint16_t)run;
-          run += S.aux[i];
+        for (uint32_t q = q0; q < q1; ++q) {
+          S.pre[q] = (uint16_t)run;
+          run += S.aux[q];
         }
         if (tid == 0) S.pre[N] = (uint16_t)tot;
       }
       __syncthreads();
       for (uint32_t k = tid; k < ncur; k += T)
         cc[k].lcount = (uint16_t)(S.pre[cc[k].begin + cc[k].count] - S.pre[cc[k].begin]);
-      __syncthreads();
       for (uint32_t i = tid; i < N; i += T) {
         const uint16_t k = S.cellid[i];
         if (k == kNoCell) {
@@ -465,7 +570,8 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
         }
         const uint32_t b = cc[k].begin;
         const uint32_t lb = (uint32_t)S.pre[i] - S.pre[b];
-        const uint32_t dst = S.aux[i] ? b + lb : b + cc[k].lcount + (i - b - lb);
+        const uint32_t L = (uint32_t)S.pre[b + cc[k].count] - S.pre[b];
+        const uint32_t dst = S.aux[i] ? b + lb : b + L + (i - b - lb);
         ordB[dst] = ordA[i];
       }
       __syncthreads();
@@ -475,7 +581,9 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
         ordB = x;
       }
 
-      // ---- 5. children
+      // ---- 6. children: one scan over the cells numbers the live children
+      // (their number is parked in the parent's mkey); then every position
+      // takes its child's number
       const int nlevel = level + 1;
       uint32_t total_live = 0;
       {
@@ -495,8 +603,8 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
       uint32_t run_out = 0;
       for (uint32_t k0 = 0; k0 < ncur; k0 += T) {
         const uint32_t k = k0 + tid;
-        LCell ch0{}, ch1{};
-        uint32_t nlive = 0;
+        LCell ch[2] = {};
+        bool live[2] = {false, false};
         if (k < ncur) {
           const LCell p = cc[k];
           const uint32_t L = p.lcount, R = p.count - L;
@@ -510,27 +618,33 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
             } else if (t.depth == 0 && nlevel >= t.max_levels) {
               set_status(t, ST_LEVEL_CAP);
             } else {
-              const LCell ch{heap, 0u, (uint16_t)cbeg[side], (uint16_t)cn[side], 0, 0, (uint8_t)stall};
-              if (nlive == 0) ch0 = ch; else ch1 = ch;
-              ++nlive;
+              ch[side] = LCell{heap, 0u, (uint16_t)cbeg[side], (uint16_t)cn[side], 0, 0, (uint8_t)stall};
+              live[side] = true;
             }
           }
         }
+        const uint32_t nlive = (uint32_t)live[0] + (uint32_t)live[1];
         uint32_t tot;
         const uint32_t ex = block_excl_scan(nlive, tmp, &tot);
-        if (nlive > 0) nc[run_out + ex] = ch0;
-        if (nlive > 1) nc[run_out + ex + 1] = ch1;
+        if (k < ncur) {
+          const uint32_t li = live[0] ? run_out + ex : kNoCell;
+          const uint32_t ri = live[1] ? run_out + ex + (live[0] ? 1u : 0u) : kNoCell;
+          if (live[0]) nc[li] = ch[0];
+          if (live[1]) nc[ri] = ch[1];
+          cc[k].mkey = li | (ri << 16);
+        }
         run_out += tot;
       }
-      for (uint32_t i = tid; i < N; i += T) S.cellid[i] = kNoCell;
       if (tid == 0) {
         s_ncur = run_out;
         s_where = (uint32_t)nwhere;
       }
       __syncthreads();
-      for (uint32_t j = warp; j < run_out; j += NW) {
-        const uint32_t b = nc[j].begin, e = b + nc[j].count;
-        for (uint32_t i = b + lane; i < e; i += 32) S.cellid[i] = (uint16_t)j;
+      for (uint32_t i = tid; i < N; i += T) {
+        const uint16_t k = S.cellid[i];
+        if (k == kNoCell) continue;
+        const uint32_t side = (i - cc[k].begin) >= cc[k].lcount ? 16u : 0u;
+        S.cellid[i] = (uint16_t)(cc[k].mkey >> side);
       }
       __syncthreads();
       which ^= 1;
