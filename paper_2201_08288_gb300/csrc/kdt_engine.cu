@@ -14,7 +14,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // Engine words.
-enum Word { W_NTILES = 0, W_BIGSEG, W_HEAD, W_NEXTBIG, W_SMALL, W_BIGPTS, W_SMALLPTS, W_OFFUSED, W_COUNT };
+enum Word { W_NTILES = 0, W_BIGSEG, W_HEAD, W_NEXTBIG, W_SMALL, W_BIGPTS, W_SMALLPTS, W_OFFUSED, W_MIDSEG, W_COUNT };
 // Per-slot words: [which][max_trees].
 enum SlotWord { S_TERM = 0, S_STATUS, S_LEVELS, S_LIVE, S_COUNT };
 
@@ -157,10 +157,10 @@ StepPlan plan_step(const StepNeeds& needs) {
   s.mkey = take((size_t)s.maxB * 4);
   s.lcount = take((size_t)s.maxB * 4);
   s.seg_w = take((size_t)s.nseg_cap * 4);
-  s.seg_beg = take((size_t)s.nseg_cap * 4);
+  s.seg_key = take((size_t)s.nseg_cap * 8);
   s.seg_med = take((size_t)s.nseg_cap * 4);
-  s.seg_cell = take((size_t)s.nseg_cap * 4);
   s.bigseg = take((size_t)s.bigseg_cap * 4);
+  s.midseg = take((size_t)s.nseg_cap * 4);
   s.slices = take((size_t)s.grid_sub * 2 * needs.slice_cells * sizeof(LCell));
   for (int b = 0; b < 2; ++b) {
     s.off[b] = take((size_t)s.off_cap * 4);
@@ -192,11 +192,12 @@ Engine::Engine(const StepPlan& plan, uint8_t* base, cudaStream_t st) : plan_(pla
   s_.tile_mm = (uint32_t*)(base + plan.tile_mm);
   s_.child_mm = (uint32_t*)(base + plan.child_mm);
   s_.seg_w = (uint32_t*)(base + plan.seg_w);
-  s_.seg_beg = (uint32_t*)(base + plan.seg_beg);
+  s_.seg_key = (const uint32_t**)(base + plan.seg_key);
   s_.seg_med = (uint32_t*)(base + plan.seg_med);
-  s_.seg_cell = (uint32_t*)(base + plan.seg_cell);
   s_.bigseg = (uint32_t*)(base + plan.bigseg);
   s_.bigseg_count = words_ + W_BIGSEG;
+  s_.midseg = (uint32_t*)(base + plan.midseg);
+  s_.midseg_count = words_ + W_MIDSEG;
   s_.tile_left = (uint32_t*)(base + plan.tile_left);
   s_.tile_loff = (uint32_t*)(base + plan.tile_loff);
   s_.next_big_count = words_ + W_NEXTBIG;
@@ -213,6 +214,7 @@ Engine::Engine(const StepPlan& plan, uint8_t* base, cudaStream_t st) : plan_(pla
   s_.off_used = words_ + W_OFFUSED;
   s_.off_cap = plan.off_cap;
   s_.bigseg_cap = plan.bigseg_cap;
+  s_.midseg_cap = plan.nseg_cap;
   s_.crow = (uint2*)(base + plan.crow);
   const uint32_t mt = std::max<uint32_t>(plan.needs.max_trees, 1);
   host_.assign(mt, TreeHost{});

@@ -54,7 +54,7 @@ struct StepPlan {
   uint32_t maxB = 0, cap_small = 0, max_tiles = 0, nseg_cap = 0, bigseg_cap = 0, grid_sub = 0, off_cap = 0;
   size_t trees = 0, words = 0, slot_words = 0, slots_list = 0, big[2] = {0, 0}, small = 0, tile_base = 0,
          seg_base = 0, tiles = 0, tile_left = 0, tile_loff = 0, tile_mm = 0, child_mm = 0, kdim = 0,
-         mkey = 0, lcount = 0, seg_w = 0, seg_beg = 0, seg_med = 0, seg_cell = 0, bigseg = 0, slices = 0,
+         mkey = 0, lcount = 0, seg_w = 0, seg_key = 0, seg_med = 0, bigseg = 0, midseg = 0, slices = 0,
          off[2] = {0, 0}, obase[2] = {0, 0}, crow = 0;
   size_t bytes = 0;
 };

@@ -29,6 +29,7 @@ constexpr int kMaxSubsets = 4096;     // r <= 4096 on the CUDA path
 constexpr int kMaxLevels = 30;        // depth / max_levels <= 30
 constexpr int kTile = 2048;           // points per tile of the multi-CTA pipeline
 constexpr int kTileThreads = 256;     // threads of the tile kernels
+constexpr int kSelTinyMax = 32;       // segments up to this size: one thread per segment
 constexpr int kSelSmallMax = 4096;    // segments up to this size: one warp per segment
 constexpr int kSubtreeThreads = 256;  // threads of a CTA of the in-shared-memory subtree kernel
 constexpr int kSubtreeWarps = kSubtreeThreads / 32;
@@ -124,15 +125,16 @@ struct StepDev {
   uint32_t* kdim;         // [ncells] key coordinate
   uint32_t* mkey;         // [ncells] split key
   uint32_t* lcount;       // [ncells] left child size
-  uint32_t* tile_mm;      // [ntiles][2][kMaxDims][2] per-tile min/max keys (widest): at the
-                          // root per tile of the cell itself, after the scatter per child side
-  uint32_t* child_mm;     // [ncells][2][kMaxDims][2] per-child min/max keys (widest)
+  uint32_t* tile_mm;      // [ntiles][2][kMaxDims][2] per-tile min/max keys of a root (widest; side 0)
+  uint32_t* child_mm;     // [ncells][2][kMaxDims][2] per-child min/max keys (widest), reduced
+                          // by the scatter with atomics
   uint32_t* seg_w;        // [nseg] points per (cell, subset)
-  uint32_t* seg_beg;      // [nseg] position of the segment in its tree's current order
+  const uint32_t** seg_key; // [nseg] first key of the segment (raw float bits, key column)
   uint32_t* seg_med;      // [nseg] lower median key
-  uint32_t* seg_cell;     // [nseg] owning cell
   uint32_t* bigseg;       // [bigseg_cap] segments larger than kSelSmallMax
   uint32_t* bigseg_count; // device word
+  uint32_t* midseg;       // [midseg_cap] segments of kSelTinyMax+1 .. kSelSmallMax points
+  uint32_t* midseg_count; // device word
   uint32_t* tile_left;    // [ntiles]
   uint32_t* tile_loff;    // [ntiles]
   Cell* next_big;         // children that stay in the multi-CTA pipeline
@@ -153,6 +155,8 @@ struct StepDev {
   uint32_t* off_used;         // device word: words of off_next handed out
   uint32_t off_cap;
   uint32_t bigseg_cap;
+  uint32_t midseg_cap;
+  uint32_t pad4;
   uint2* crow;                // [ncells][2] (slot, row of off_next) of each big child, else kNoRow
 };
 

@@ -58,7 +58,7 @@ struct SubMeta {
   uint32_t* out_perm;  // final permutation (terminal children)
   int32_t* status;
   int64_t n;
-  uint32_t cell_begin, cell_count, tile, sub, mcnt, T, dim, mkey, L, loff, tile_start;
+  uint32_t cell_begin, cell_count, cell_idx, tile, sub, mcnt, T, dim, mkey, L, loff, tile_start;
   uint32_t row[2];     // rows of the children's subset offsets (kNoRow: not a big child)
   uint32_t prev_sub;   // subset of the point before the sub-tile (~0u at the cell's start)
   uint32_t r, subset_mode, sid_bytes, sid_ph, tn;
@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
   __shared__ SubMeta meta[2];
   __shared__ uint32_t wcnt[kMaxItems][kCW];
   __shared__ uint32_t sedge[kMaxItems][kCW];  // subset of each warp's last point per round
-  __shared__ uint32_t tmm[2][kMaxDims][2];    // per tile and child: min / max key per coordinate
+  __shared__ uint32_t tmm[2][kMaxDims][2];    // this CTA's run of tiles of one cell: per child,
+                                              // min / max key per coordinate
   __shared__ uint32_t s_fail;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ntiles = *s.ntiles_total;
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           m.n = tg.n;
           m.cell_begin = c.begin;
           m.cell_count = c.count;
+          m.cell_idx = tl.x;
           m.tile = tile;
           m.sub = sub;
           m.mcnt = mcnt;
@@ -238,6 +240,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
   uint32_t fphase[2] = {0u, 0u};
   uint32_t lnext = 0, rnext = 0;
   bool saw_nan = false;
+  bool fresh = true;  // tmm holds nothing yet of the current cell
   uint32_t k = 0;
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     for (bool more = true; more; ++k) {
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       if (m.sub == m.tile_start) {
         lnext = cbeg + m.loff;
         rnext = cbeg + L + (m.tile_start - m.loff);
-        if (want_mm)
+        if (want_mm && fresh)
           for (int j = tid; j < 4 * d; j += kCT) {
             const int side = j / (2 * d), l = (j / 2) % d, which = j & 1;
             tmm[side][l][which] = which ? 0u : 0xffffffffu;
@@ -422,10 +425,18 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         if (saw_nan) atomicCAS(m.status, ST_OK, ST_NAN_INPUT);
         saw_nan = false;
         if (want_mm) {
-          named_sync(kConsumerBar, kCT);
-          for (int j = tid; j < 4 * d; j += kCT) {
-            const int side = j / (2 * d), l = (j / 2) % d, which = j & 1;
-            s.tile_mm[(((size_t)m.tile * 2 + side) * kMaxDims + l) * 2 + which] = tmm[side][l][which];
+          // keep reducing while this CTA's next tile is of the same cell;
+          // else add the run's min / max to the cell's with atomics
+          const uint32_t nt = tile + gridDim.x;
+          const bool same = nt < ntiles && s.tiles[nt].x == m.cell_idx;
+          fresh = !same;
+          if (!same) {
+            named_sync(kConsumerBar, kCT);
+            for (int j = tid; j < 4 * d; j += kCT) {
+              const int side = j / (2 * d), l = (j / 2) % d, which = j & 1;
+              uint32_t* dst = &s.child_mm[(((size_t)m.cell_idx * 2 + side) * kMaxDims + l) * 2 + which];
+              if (which) atomicMax(dst, tmm[side][l][which]); else atomicMin(dst, tmm[side][l][which]);
+            }
           }
         }
       }

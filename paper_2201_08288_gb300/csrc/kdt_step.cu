@@ -83,6 +83,7 @@ __global__ void k_prep(const TreeDev* trees, StepDev s) {
     s.seg_base[s.ncells] = seg_run;
     *s.ntiles_total = tile_run;
     *s.bigseg_count = 0;
+    *s.midseg_count = 0;
   }
 }
 
@@ -361,32 +362,6 @@ __global__ void k_pick_dim(const TreeDev* trees, StepDev s) {
 
 // ------------------------------------------------------------ segments
 
-// One CTA per cell: the position range of every (cell, subset) segment from
-// the cell's subset offsets, and the list of segments too large for a single
-// warp. Offsets are clamped to the cell, so a damaged table cannot send a
-// later kernel outside it (it is reported instead).
-__global__ void k_segs(const TreeDev* trees, StepDev s) {
-  const uint32_t c = blockIdx.x;
-  const Cell cell = s.cells[c];
-  const TreeDev& t = trees[cell.tree];
-  const uint32_t r = (uint32_t)t.r;
-  const uint32_t* off = cell.level == 0 ? t.root_off : s.off_cur + s.obase_cur[c];
-  const uint32_t g0 = s.seg_base[c];
-  if (threadIdx.x == 0 && (off[0] != 0u || off[r] != cell.count)) set_status(t, ST_INTERNAL);
-  for (uint32_t j = threadIdx.x; j < r; j += blockDim.x) {
-    const uint32_t a = min(off[j], cell.count), b = min(off[j + 1], cell.count);
-    if (b < a) set_status(t, ST_INTERNAL);
-    const uint32_t w = b >= a ? b - a : 0u;
-    s.seg_beg[g0 + j] = cell.begin + a;
-    s.seg_w[g0 + j] = w;
-    s.seg_cell[g0 + j] = c;
-    if (w > (uint32_t)kSelSmallMax) {
-      const uint32_t k = atomicAdd(s.bigseg_count, 1u);
-      if (k < s.bigseg_cap) s.bigseg[k] = g0 + j; else set_status(t, ST_INTERNAL);
-    }
-  }
-}
-
 // Key column of a cell (raw float bits; ord_key is applied on every load).
 __device__ __forceinline__ const uint32_t* key_column(const TreeDev& t, const Cell& cell, uint32_t dim) {
   return (const uint32_t*)(src_cols(t, cell.level) + (int64_t)dim * t.n);
@@ -394,120 +369,214 @@ __device__ __forceinline__ const uint32_t* key_column(const TreeDev& t, const Ce
 
 __device__ __forceinline__ uint32_t kload(const uint32_t* p) { return ord_key(__uint_as_float(__ldg(p))); }
 
+
+// One CTA per cell (after its key coordinate is known): size and first key
+// of every (cell, subset) segment from the cell's subset offsets, and the
+// lists of segments for the warp and CTA selects. Offsets are clamped to the
+// cell, so a damaged table cannot send a later kernel outside it (it is
+// reported instead).
+__global__ void k_segs(const TreeDev* trees, StepDev s) {
+  const uint32_t c = blockIdx.x;
+  const Cell cell = s.cells[c];
+  const TreeDev& t = trees[cell.tree];
+  const uint32_t r = (uint32_t)t.r;
+  const uint32_t* off = cell.level == 0 ? t.root_off : s.off_cur + s.obase_cur[c];
+  const uint32_t g0 = s.seg_base[c];
+  const uint32_t* kc = key_column(t, cell, s.kdim[c]) + cell.begin;
+  if (threadIdx.x == 0 && (off[0] != 0u || off[r] != cell.count)) set_status(t, ST_INTERNAL);
+  for (uint32_t j = threadIdx.x; j < r; j += blockDim.x) {
+    const uint32_t a = min(off[j], cell.count), b = min(off[j + 1], cell.count);
+    if (b < a) set_status(t, ST_INTERNAL);
+    const uint32_t w = b >= a ? b - a : 0u;
+    s.seg_key[g0 + j] = kc + a;
+    s.seg_w[g0 + j] = w;
+    if (w > (uint32_t)kSelSmallMax) {
+      const uint32_t k = atomicAdd(s.bigseg_count, 1u);
+      if (k < s.bigseg_cap) s.bigseg[k] = g0 + j; else set_status(t, ST_INTERNAL);
+    } else if (w > (uint32_t)kSelTinyMax) {
+      const uint32_t k = atomicAdd(s.midseg_count, 1u);
+      if (k < s.midseg_cap) s.midseg[k] = g0 + j; else set_status(t, ST_INTERNAL);
+    }
+  }
+}
+
 // ------------------------------------------------------------ selection
 
-// Exact key of 0-based rank `rank` among the keys of raw[0..w) by 8-bit MSD
-// radix select, one warp, histogram `hist` (256 words of shared memory owned
-// by the warp).
-__device__ uint32_t warp_radix_select(const uint32_t* keys, uint32_t w, uint32_t rank, uint32_t* hist) {
-  const int lane = threadIdx.x & 31;
-  uint32_t prefix = 0, mask = 0;
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int i = lane; i < 256; i += 32) hist[i] = 0;
-    __syncwarp();
-    uint32_t i = lane;
-    for (; i + 96 < w; i += 128) {
-      const uint32_t k0 = kload(keys + i), k1 = kload(keys + i + 32), k2 = kload(keys + i + 64),
-                     k3 = kload(keys + i + 96);
-      if ((k0 & mask) == prefix) atomicAdd(&hist[(k0 >> shift) & 255u], 1u);
-      if ((k1 & mask) == prefix) atomicAdd(&hist[(k1 >> shift) & 255u], 1u);
-      if ((k2 & mask) == prefix) atomicAdd(&hist[(k2 >> shift) & 255u], 1u);
-      if ((k3 & mask) == prefix) atomicAdd(&hist[(k3 >> shift) & 255u], 1u);
-    }
-    for (; i < w; i += 32) {
-      const uint32_t k = kload(keys + i);
-      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
-    }
-    __syncwarp();
-    uint32_t below;
-    const uint32_t digit = warp_find_digit(hist, rank, &below);
-    rank -= below;
-    prefix |= digit << shift;
-    mask |= 255u << shift;
-    __syncwarp();
-  }
-  return prefix;
-}
-
-// Lower median of one small segment (w <= 32) by counting ranks in registers.
-__device__ __forceinline__ uint32_t warp_rank_median(const uint32_t* keys, uint32_t w) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t k = (uint32_t)lane < w ? kload(keys + lane) : 0xffffffffu;
+// Lower median of a segment of w <= N keys by one thread: bitonic sorting
+// network over N registers (keys past w padded with the largest key).
+template <int N>
+__device__ __forceinline__ uint32_t thread_lower_median(const uint32_t* keys, uint32_t w) {
+  uint32_t v[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = (uint32_t)i < w ? kload(keys + i) : 0xffffffffu;
+#pragma unroll
+  for (int size = 2; size <= N; size <<= 1)
+#pragma unroll
+    for (int j = size >> 1; j > 0; j >>= 1)
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int p = i ^ j;
+        if (p > i) {
+          const uint32_t lo = min(v[i], v[p]), hi = max(v[i], v[p]);
+          if ((i & size) == 0) {
+            v[i] = lo;
+            v[p] = hi;
+          } else {
+            v[i] = hi;
+            v[p] = lo;
+          }
+        }
+      }
   const uint32_t want = (w - 1) / 2;
-  uint32_t rk = 0;
-  for (uint32_t j = 0; j < w; ++j) {
-    const uint32_t kj = __shfl_sync(0xffffffffu, k, j);
-    rk += (kj < k) || (kj == k && (int)j < lane);
-  }
-  const unsigned hit = __ballot_sync(0xffffffffu, (uint32_t)lane < w && rk == want);
-  return __shfl_sync(0xffffffffu, k, __ffs(hit) - 1);
+  uint32_t med = v[0];
+#pragma unroll
+  for (int i = 1; i < N; ++i)
+    if ((uint32_t)i == want) med = v[i];
+  return med;
 }
 
-// One warp per segment of at most kSelSmallMax points; warps stride over the
-// segments of the step (their number is read from the device).
-__global__ void __launch_bounds__(256) k_select_small(const TreeDev* trees, StepDev s) {
-  __shared__ uint32_t hist[8][256];
-  const int warp = threadIdx.x >> 5;
+// One thread per segment of at most kSelTinyMax points (threads stride over
+// the segments of the step).
+__global__ void __launch_bounds__(256) k_select_tiny(const TreeDev* trees, StepDev s) {
   const uint32_t nseg = s.seg_base[s.ncells];
-  for (uint32_t g = blockIdx.x * 8u + (uint32_t)warp; g < nseg; g += gridDim.x * 8u) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nseg; g += gridDim.x * blockDim.x) {
     const uint32_t w = s.seg_w[g];
-    if (w == 0 || w > (uint32_t)kSelSmallMax) continue;
-    const uint32_t c = s.seg_cell[g];
-    const Cell cell = s.cells[c];
-    const uint32_t* keys = key_column(trees[cell.tree], cell, s.kdim[c]) + s.seg_beg[g];
+    if (w == 0 || w > (uint32_t)kSelTinyMax) continue;
+    const uint32_t* keys = s.seg_key[g];
     uint32_t med;
-    if (w <= 32)
-      med = warp_rank_median(keys, w);
+    if (w <= 8)
+      med = thread_lower_median<8>(keys, w);
+    else if (w <= 16)
+      med = thread_lower_median<16>(keys, w);
     else
-      med = warp_radix_select(keys, w, (w - 1) / 2, hist[warp]);
-    if ((threadIdx.x & 31) == 0) s.seg_med[g] = med;
+      med = thread_lower_median<32>(keys, w);
+    s.seg_med[g] = med;
   }
 }
 
-// One CTA per listed large segment: the same radix select with a CTA-wide
-// histogram.
-__global__ void __launch_bounds__(256) k_select_big(const TreeDev* trees, StepDev s) {
-  if (blockIdx.x >= *s.bigseg_count) return;
-  __shared__ uint32_t hist[256];
-  __shared__ uint32_t bcast[2];
-  const uint32_t g = s.bigseg[blockIdx.x];
-  const uint32_t w = s.seg_w[g];
-  const uint32_t c = s.seg_cell[g];
-  const Cell cell = s.cells[c];
-  const uint32_t* keys = key_column(trees[cell.tree], cell, s.kdim[c]) + s.seg_beg[g];
-  uint32_t rank = (w - 1) / 2, prefix = 0, mask = 0;
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    uint32_t i = threadIdx.x;
-    for (; i + 7 * 256 < w; i += 8 * 256) {
-      uint32_t k[8];
+// Lower median of w <= 32K keys by one warp: bitonic sorting network over
+// K registers per lane (element e = k * 32 + lane; keys past w padded with
+// the largest key), then the element of rank (w-1)/2.
+template <int K>
+__device__ uint32_t warp_bitonic_median(const uint32_t* keys, uint32_t w) {
+  const int lane = threadIdx.x & 31;
+  uint32_t v[K];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) k[q] = kload(keys + i + q * 256);
+  for (int k = 0; k < K; ++k) {
+    const uint32_t e = (uint32_t)(k * 32 + lane);
+    v[k] = e < w ? kload(keys + e) : 0xffffffffu;
+  }
+  constexpr int N = 32 * K;
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if ((k[q] & mask) == prefix) atomicAdd(&hist[(k[q] >> shift) & 255u], 1u);
-    }
-    for (; i < w; i += 256) {
-      const uint32_t k = kload(keys + i);
-      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      uint32_t below;
-      const uint32_t digit = warp_find_digit(hist, rank, &below);
-      if (threadIdx.x == 0) {
-        bcast[0] = digit;
-        bcast[1] = below;
+  for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+    for (int j = size >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int e = k * 32 + lane;
+        const bool asc = (e & size) == 0;
+        if (j >= 32) {
+          const int kk = k ^ (j >> 5);
+          if (k < kk) {
+            const uint32_t lo = min(v[k], v[kk]), hi = max(v[k], v[kk]);
+            v[k] = asc ? lo : hi;
+            v[kk] = asc ? hi : lo;
+          }
+        } else {
+          const uint32_t o = __shfl_xor_sync(0xffffffffu, v[k], j);
+          const bool lower = (lane & j) == 0;
+          v[k] = (lower == asc) ? min(v[k], o) : max(v[k], o);
+        }
       }
     }
-    __syncthreads();
-    rank -= bcast[1];
-    prefix |= bcast[0] << shift;
-    mask |= 255u << shift;
-    __syncthreads();
   }
-  if (threadIdx.x == 0) s.seg_med[g] = prefix;
+  const uint32_t want = (w - 1) / 2;
+  uint32_t x = v[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k)
+    if ((uint32_t)k == want / 32u) x = v[k];
+  return __shfl_sync(0xffffffffu, x, want % 32u);
+}
+
+// One warp per listed segment of kSelTinyMax+1 .. kSelSmallMax points: up to
+// 256 keys sorted in registers; larger segments: keys staged once in shared
+// memory (up to 1024 of them), then a radix select over the bits where they
+// differ.
+__global__ void __launch_bounds__(256) k_select_small(const TreeDev* trees, StepDev s) {
+  __shared__ uint32_t hist[8][256];
+  __shared__ uint32_t stage[8][1024];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t cnt = min(*s.midseg_count, s.midseg_cap);
+  for (uint32_t j = blockIdx.x * 8u + (uint32_t)warp; j < cnt; j += gridDim.x * 8u) {
+    const uint32_t g = s.midseg[j];
+    const uint32_t w = s.seg_w[g];
+    const uint32_t* keys = s.seg_key[g];
+    uint32_t med;
+    if (w <= 64u) {
+      med = warp_bitonic_median<2>(keys, w);
+    } else if (w <= 128u) {
+      med = warp_bitonic_median<4>(keys, w);
+    } else if (w <= 256u) {
+      med = warp_bitonic_median<8>(keys, w);
+    } else if (w <= 1024u) {
+      uint32_t* st = stage[warp];
+      for (uint32_t i = lane; i < w; i += 32) st[i] = kload(keys + i);
+      __syncwarp();
+      med = warp_weighted_select<true>(w, (w - 1) / 2, hist[warp], [&](uint32_t i) { return st[i]; },
+                                       [](uint32_t) { return 1u; });
+    } else {
+      med = warp_weighted_select<true>(w, (w - 1) / 2, hist[warp], [&](uint32_t i) { return kload(keys + i); },
+                                       [](uint32_t) { return 1u; });
+    }
+    if (lane == 0) s.seg_med[g] = med;
+    __syncwarp();
+  }
+}
+
+// CTAs stride over the listed segments above kSelSmallMax points: 8-bit MSD
+// radix select with a CTA-wide histogram, keys read from global memory.
+__global__ void __launch_bounds__(256) k_select_big(const TreeDev* trees, StepDev s) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t bcast[2];
+  const uint32_t cnt = min(*s.bigseg_count, s.bigseg_cap);
+  for (uint32_t jb = blockIdx.x; jb < cnt; jb += gridDim.x) {
+    const uint32_t g = s.bigseg[jb];
+    const uint32_t w = s.seg_w[g];
+    const uint32_t* keys = s.seg_key[g];
+    uint32_t rank = (w - 1) / 2, prefix = 0, mask = 0;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+      __syncthreads();
+      uint32_t i = threadIdx.x;
+      for (; i + 7 * 256 < w; i += 8 * 256) {
+        uint32_t k[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) k[q] = kload(keys + i + q * 256);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if ((k[q] & mask) == prefix) atomicAdd(&hist[(k[q] >> shift) & 255u], 1u);
+      }
+      for (; i < w; i += 256) {
+        const uint32_t k = kload(keys + i);
+        if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+      }
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        uint32_t below;
+        const uint32_t digit = warp_find_digit(hist, rank, &below);
+        if (threadIdx.x == 0) {
+          bcast[0] = digit;
+          bcast[1] = below;
+        }
+      }
+      __syncthreads();
+      rank -= bcast[1];
+      prefix |= bcast[0] << shift;
+      mask |= 255u << shift;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) s.seg_med[g] = prefix;
+  }
 }
 
 // One CTA per cell: count-weighted lower median of the segment medians: the
@@ -604,34 +673,41 @@ __global__ void k_part_scan(StepDev s) {
   if (threadIdx.x == 0) s.lcount[c] = run;
 }
 
-// Grid (cell, side, coordinate): reduce the scatter's tile partials to each
-// child's min and max key per coordinate (widest spread only).
-__global__ void k_child_mm(const TreeDev* trees, StepDev s) {
-  const uint32_t c = blockIdx.x, side = blockIdx.y, l = blockIdx.z;
+// One warp per cell (widest spread): the key coordinate of each big child
+// from its min and max key per coordinate (reduced by the scatter): the
+// largest range (double)max - (double)min, 0 for equal keys, lowest
+// coordinate on ties.
+__global__ void __launch_bounds__(256) k_child_dims(const TreeDev* trees, StepDev s) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t c = blockIdx.x * 8u + (uint32_t)warp;
+  if (c >= s.ncells) return;
   const Cell cell = s.cells[c];
   const TreeDev& t = trees[cell.tree];
-  if (t.key_rule != KEY_WIDEST || (int)l >= t.d) return;
-  __shared__ uint32_t red[2][8];
-  const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
-  uint32_t lo = 0xffffffffu, hi = 0u;
-  for (uint32_t j = tb + threadIdx.x; j < te; j += blockDim.x) {
-    lo = min(lo, s.tile_mm[(((size_t)j * 2 + side) * kMaxDims + l) * 2 + 0]);
-    hi = max(hi, s.tile_mm[(((size_t)j * 2 + side) * kMaxDims + l) * 2 + 1]);
-  }
-  lo = __reduce_min_sync(0xffffffffu, lo);
-  hi = __reduce_max_sync(0xffffffffu, hi);
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = lo;
-    red[1][threadIdx.x >> 5] = hi;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      lo = min(lo, red[0][w]);
-      hi = max(hi, red[1][w]);
+  if (t.key_rule != KEY_WIDEST) return;
+  const int d = t.d;
+  for (int side = 0; side < 2; ++side) {
+    const uint2 cr = s.crow[2 * c + side];
+    if (cr.x == kNoRow) continue;
+    double rb = -1.0;
+    int ib = 0;
+    for (int l = lane; l < d; l += 32) {
+      const uint2 mm = *(const uint2*)&s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2];
+      const double range = key_range(mm.x, mm.y);
+      if (range > rb) {
+        rb = range;
+        ib = l;
+      }
     }
-    s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 0] = lo;
-    s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 1] = hi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double orb = __shfl_xor_sync(0xffffffffu, rb, o);
+      const int oib = __shfl_xor_sync(0xffffffffu, ib, o);
+      if (orb > rb || (orb == rb && oib < ib)) {
+        rb = orb;
+        ib = oib;
+      }
+    }
+    if (lane == 0) s.next_big[cr.x].dim = (int16_t)ib;
   }
 }
 
@@ -652,6 +728,11 @@ __global__ void k_classify(const TreeDev* trees, StepDev s) {
   const uint32_t cb[2] = {cell.begin, cell.begin + L};
   const uint32_t cc[2] = {L, R};
   int live_delta = -1;  // this cell is done; each child that still needs splitting adds one
+  if (t.key_rule == KEY_WIDEST)  // identities for the scatter's min / max reductions
+    for (int j = 0; j < 4 * t.d; ++j) {
+      const int side = j / (2 * t.d), l = (j / 2) % t.d, which = j & 1;
+      s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + which] = which ? 0u : 0xffffffffu;
+    }
   for (int side = 0; side < 2; ++side) {
     uint2 cr = make_uint2(kNoRow, kNoRow);
     const uint32_t heap = 2u * cell.heap + 1u + (uint32_t)side;
@@ -684,31 +765,6 @@ __global__ void k_classify(const TreeDev* trees, StepDev s) {
   if (live_delta) atomicAdd(t.live, live_delta);
 }
 
-// One thread per cell (widest spread): the key coordinate of each big child
-// from the min and max keys the scatter reduced for it.
-__global__ void k_next_dims(const TreeDev* trees, StepDev s) {
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= s.ncells) return;
-  const Cell cell = s.cells[c];
-  const TreeDev& t = trees[cell.tree];
-  if (t.key_rule != KEY_WIDEST) return;
-  for (int side = 0; side < 2; ++side) {
-    const uint2 cr = s.crow[2 * c + side];
-    if (cr.x == kNoRow) continue;
-    int best = 0;
-    double best_range = -1.0;
-    for (int l = 0; l < t.d; ++l) {
-      const double range = key_range(s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 0],
-                                     s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2 + 1]);
-      if (range > best_range) {
-        best_range = range;
-        best = l;
-      }
-    }
-    s.next_big[cr.x].dim = (int16_t)best;
-  }
-}
-
 }  // namespace
 
 // ------------------------------------------------------------ launcher
@@ -729,25 +785,29 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
     { TraceScope ts(K_PS_OFFSETS, st); k_ps_offsets<<<nc, 1024, 0, st>>>(trees, s); }
     { TraceScope ts(K_PS_MOVE, st, points); k_ps_move<<<max_tiles, kPsThreads, kPsSmemBytes, st>>>(trees, s); }
   }
-  { TraceScope ts(K_SEGS, st); k_segs<<<nc, 256, 0, st>>>(trees, s); }
   if (need_root_dims) {
     { TraceScope ts(K_MINMAX, st, points); k_minmax<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
     { TraceScope ts(K_PICK_DIM, st); k_pick_dim<<<nc, 256, 0, st>>>(trees, s); }
   }
+  { TraceScope ts(K_SEGS, st); k_segs<<<nc, 256, 0, st>>>(trees, s); }
+  {
+    TraceScope ts(K_SELECT_TINY, st, points);
+    k_select_tiny<<<std::max<uint32_t>(1, std::min<uint32_t>((nseg + 255) / 256, sms * 16u)), 256, 0, st>>>(trees, s);
+  }
   {
     TraceScope ts(K_SELECT_SMALL, st, points);
-    k_select_small<<<std::min<uint32_t>((nseg + 7) / 8, 152u * 32u), 256, 0, st>>>(trees, s);
+    k_select_small<<<std::max<uint32_t>(1, std::min<uint32_t>((nseg + 7) / 8, sms * 8u)), 256, 0, st>>>(trees, s);
   }
-  if (max_bigseg) { TraceScope ts(K_SELECT_BIG, st); k_select_big<<<max_bigseg, 256, 0, st>>>(trees, s); }
+  if (max_bigseg) {
+    TraceScope ts(K_SELECT_BIG, st);
+    k_select_big<<<std::max<uint32_t>(1, std::min<uint32_t>(max_bigseg, sms * 4u)), 256, 0, st>>>(trees, s);
+  }
   { TraceScope ts(K_COMBINE, st); k_combine<<<nc, 256, 0, st>>>(trees, s); }
   { TraceScope ts(K_PART_COUNT, st, points); k_part_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
   { TraceScope ts(K_PART_SCAN, st); k_part_scan<<<nc, 1024, 0, st>>>(s); }
   { TraceScope ts(K_CLASSIFY, st); k_classify<<<(nc + 255) / 256, 256, 0, st>>>(trees, s); }
   launch_scatter(trees, s, max_tiles, 2 * sms, points, st);
-  if (any_widest) {
-    { TraceScope ts(K_CHILD_MM, st); k_child_mm<<<dim3(nc, 2, max_d), 256, 0, st>>>(trees, s); }
-    { TraceScope ts(K_NEXT_DIMS, st); k_next_dims<<<(nc + 255) / 256, 256, 0, st>>>(trees, s); }
-  }
+  if (any_widest) { TraceScope ts(K_CHILD_DIMS, st); k_child_dims<<<(nc + 7) / 8, 256, 0, st>>>(trees, s); }
 }
 
 }  // namespace kdt
