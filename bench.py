@@ -66,9 +66,11 @@ def bytes_per_point(kernel: str, d: int, sid_bytes: int, subset_mode: int) -> fl
 
 def model_bytes_per_point_level(d: int, sid_bytes: int, subset_mode: int) -> float:
     """Bytes each level must move per point (SoA ping-pong model): the key
-    column read once for the selection, read+write of all columns and the
+    column read for the selection, the subset-id source (explicit ids, or the
+    permutation the id is derived from), read+write of all columns and the
     permutation, read+write of an explicit id column."""
-    return 4 + 8 * (d + 1) + 2 * (sid_bytes if subset_mode == 2 else 0)
+    s_sel = sid_bytes if subset_mode == 2 else 4
+    return 4 + s_sel + 8 * (d + 1) + 2 * (sid_bytes if subset_mode == 2 else 0)
 
 
 class Clocks:
@@ -199,13 +201,162 @@ def run_reference(args) -> None:
     }))
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
+
+
+def run_batched(args, dev, kdt) -> dict:
+    """Independent trees of the batched recipe (n log-uniform in [2^8, 2^20],
+    d in {2,3,8,16}, uniform or 8-cluster mixture, r in {4,16,64} by index mod
+    r, cyclic, leaf <= 32) built together by kdt_build_batched; the same trees
+    built one by one with kdt_build for comparison."""
+    import torch
+    from paper_2201_08288_gb300 import workloads as W
+    specs = W.config4_batch(num_trees=args.trees)
+    items = []
+    for s in specs:
+        items.append(dict(points=s.points_device(dev), r=s.r, subset_mode=0, depth=0, leaf_size=32,
+                          max_levels=s.max_levels, key_rule=0))
+    descs, outs = kdt.make_descs(items)
+    ws = torch.empty(kdt.kdt_workspace_size_batched(descs), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        trees, st = kdt.kdt_build_batched(items, workspace=ws, outputs=outs, descs=descs, stream=stream)
+    torch.cuda.synchronize()
+    assert all(x == 0 for x in st), st
+    units = sum(int(s.n) * t.levels for s, t in zip(specs, trees))
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    launches0 = kdt.kdt_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        kdt.kdt_build_batched(items, workspace=ws, outputs=outs, descs=descs, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = kdt.kdt_launch_count() - launches0
+    clk = clocks.stop()
+    del ws
+    torch.cuda.empty_cache()
+    # the same trees, one kdt_build each (workspace sized for the largest)
+    big = max(range(len(items)), key=lambda i: specs[i].n * (specs[i].d + 1))
+    sizes = [kdt.kdt_workspace_size(kdt.make_params(int(s.n), s.d, r=s.r, subset_mode=0, depth=0, leaf_size=32,
+                                                    max_levels=s.max_levels)) for s in specs]
+    ws1 = torch.empty(max(sizes), dtype=torch.uint8, device=dev)
+    for i in range(min(64, len(items))):
+        it = items[i]
+        kdt.kdt_build(it["points"], workspace=ws1, outputs=outs[i], stream=stream,
+                      **{k: v for k, v in it.items() if k != "points"})
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, it in enumerate(items):
+        kdt.kdt_build(it["points"], workspace=ws1, outputs=outs[i], stream=stream,
+                      **{k: v for k, v in it.items() if k != "points"})
+    torch.cuda.synchronize()
+    solo_s = time.perf_counter() - t0
+    value = args.steps * units / (ms / 1e3)
+    solo = units / solo_s
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"batched_{len(items)}_trees_n2^8..2^20_d2-16_mod_r4-64_leaf32",
+                       "points": int(sum(s.n for s in specs)), "points_x_levels": units,
+                       "parallelism": "replicas1"},
+            "solo_loop": {"value": solo, "unit": UNIT, "ms": 1e3 * solo_s,
+                          "what": "the same trees, one kdt_build call each, in sequence"},
+            "batched_vs_solo": value / solo, "gpu_launches": launches, "clocks": clk}
+
+
+def run_serving(args, dev, kdt) -> dict:
+    """A Poisson stream of build requests (n log-uniform in [2^10, 2^24],
+    d in {3,16}, uniform or 8-cluster mixture, r=32 by index mod r, leaf <= 64)
+    submitted to a kdt.Server with a 64 GB budget; each request's points are
+    drawn on the device when it arrives. The arrival rate is `load` times the
+    server's saturated capacity (the first 200 requests submitted at once).
+    Reports p50/p99 latency (submit to completion) and throughput against the
+    same requests built one by one."""
+    import torch
+    from paper_2201_08288_gb300 import workloads as W
+    stream = torch.cuda.current_stream(dev)
+    _, specs = W.config5_stream(num_requests=args.requests, rate=1.0)
+    kw_of = lambda s: dict(r=32, subset_mode=0, depth=0, leaf_size=64, max_levels=s.max_levels, key_rule=0)
+    sample = specs[:min(200, len(specs))]
+    # solo: the sample built one by one
+    ws1 = torch.empty(max(kdt.kdt_workspace_size(kdt.make_params(int(s.n), s.d, **kw_of(s))) for s in sample),
+                      dtype=torch.uint8, device=dev)
+    pts_s = [s.points_device(dev) for s in sample]
+    for p_, s in zip(pts_s[:8], sample[:8]):
+        kdt.kdt_build(p_, workspace=ws1, stream=stream, **kw_of(s))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solo_units = 0
+    for p_, s in zip(pts_s, sample):
+        t = kdt.kdt_build(p_, workspace=ws1, stream=stream, **kw_of(s))
+        solo_units += int(s.n) * t.levels
+    torch.cuda.synchronize()
+    solo_s = time.perf_counter() - t0
+    del ws1
+    torch.cuda.empty_cache()
+    with kdt.Server(64 << 30, 256) as sv:
+        # saturated capacity: the sample submitted at once
+        t0 = time.perf_counter()
+        tks = [sv.submit(dict(points=p_, **kw_of(s))) for p_, s in zip(pts_s, sample)]
+        for tk in tks:
+            assert sv.poll(tk)[0] == 0
+        capacity = len(sample) / (time.perf_counter() - t0)
+        del pts_s, tks
+        torch.cuda.empty_cache()
+        rate = args.load * capacity
+        arrivals, specs = W.config5_stream(num_requests=args.requests, rate=rate)
+        lat, units, backlog_max = [], 0, 0
+        live = {}
+        t_start = time.perf_counter()
+
+        def reap(wait):
+            nonlocal units
+            for tk in list(live):
+                r = sv.poll(tk, -1 if wait else 0)
+                if r is not None:
+                    assert r[0] == 0, r[0]
+                    lat.append(r[2])
+                    units += int(live.pop(tk).n) * r[1].levels
+
+        for i, s in enumerate(specs):
+            reap(False)  # once per arrival: polling takes the server's lock
+            ahead = arrivals[i] - (time.perf_counter() - t_start)
+            if ahead > 0:
+                time.sleep(ahead)
+            if len(live) > 512:
+                raise SystemExit("serving: more than 512 requests outstanding; the arrival rate exceeds capacity")
+            live[sv.submit(dict(points=s.points_device(dev), **kw_of(s)))] = s
+            backlog_max = max(backlog_max, len(live))
+        reap(True)
+        wall = time.perf_counter() - t_start
+        info = sv.stats()
+    return {"metric": METRIC, "value": units / wall, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"serving_{len(specs)}_requests_poisson_n2^10..2^24_d3or16_mod_r32_leaf64",
+                       "rate_per_s": rate, "load": args.load, "capacity_per_s": capacity, "mem_budget_gb": 64},
+            "latency_ms": {"p50": _pct(lat, 0.5), "p99": _pct(lat, 0.99), "max": max(lat)},
+            "peak_in_flight": info["peak_in_flight"], "outstanding_max": backlog_max,
+            "solo": {"value": solo_units / solo_s, "unit": UNIT, "requests_per_s": len(sample) / solo_s,
+                     "what": f"the first {len(sample)} requests, one kdt_build each, back to back"},
+            "served_vs_solo": (units / wall) / (solo_units / solo_s)}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c3s"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c3s", "c4", "c5"])
+    ap.add_argument("--trees", type=int, default=4096, help="c4: number of trees")
+    ap.add_argument("--requests", type=int, default=20000, help="c5: number of requests")
+    ap.add_argument("--load", type=float, default=0.7, help="c5: arrival rate / solo capacity")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -230,6 +381,11 @@ def main() -> None:
     if dist:
         dist.barrier()
     kdt.load_library()
+    if args.workload in ("c4", "c5"):
+        res = run_batched(args, dev, kdt) if args.workload == "c4" else run_serving(args, dev, kdt)
+        if rank == 0:
+            print(json.dumps(res))
+        return
 
     spec, kw = workload(args.workload, rank)
     pts = spec.points_device(dev)

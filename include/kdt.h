@@ -187,8 +187,13 @@ typedef struct kdt_server_info {
 /* Create a server on the current device. Errors: KDT_ERR_INVALID_ARG (budget
  * below 64 MiB, max_trees_in_flight < 1), KDT_ERR_OOM, KDT_ERR_CUDA. */
 kdt_status kdt_server_create(size_t mem_budget_bytes, int32_t max_trees_in_flight, kdt_server **out);
-/* Queue a build. *ticket identifies it. KDT_ERR_CAPACITY: the request can
- * never fit the budget; KDT_ERR_INVALID_ARG as kdt_build. */
+/* Queue a build. *ticket identifies it. The server reads the request's
+ * device buffers on its own stream at some later time: the points (and
+ * subset ids) must already be complete when kdt_server_submit is called (for
+ * example, synchronise the stream that wrote them), and all buffers of the
+ * request must stay valid until kdt_server_poll reports it finished.
+ * KDT_ERR_CAPACITY: the request can never fit the budget; KDT_ERR_INVALID_ARG
+ * as kdt_build. */
 kdt_status kdt_server_submit(kdt_server *s, const kdt_tree_desc *request, uint64_t *ticket);
 /* Wait up to wait_ms (< 0: forever, 0: do not wait) for a ticket. KDT_OK: the
  * request finished; *result holds its build status, *levels its L and

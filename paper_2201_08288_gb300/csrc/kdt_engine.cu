@@ -342,7 +342,15 @@ kdt_status Engine::tick() {
     s_.off_next = off_[cur_ ^ 1];
     s_.obase_next = obase_[cur_ ^ 1];
     const uint64_t nseg_bound = std::min<uint64_t>((uint64_t)big_count_ * KDT_MAX_SUBSETS, plan_.nseg_cap);
-    launch_big_step(trees_, s_, plan_.max_tiles, (uint32_t)nseg_bound, plan_.bigseg_cap, has_roots, root_dims_,
+    // tiles of this step: at most one per kTile points plus one per cell (a
+    // tight launch size; the plan's max_tiles is the capacity of a full forest)
+    // (the point counter is one device word: trust it only while it cannot wrap)
+    const uint32_t tiles_bound =
+        plan_.needs.points > 0xffffffffull
+            ? plan_.max_tiles
+            : (uint32_t)std::min<uint64_t>(big_points_ / (uint64_t)kTile + (uint64_t)big_count_ + 1,
+                                           (uint64_t)plan_.max_tiles);
+    launch_big_step(trees_, s_, tiles_bound, (uint32_t)nseg_bound, plan_.bigseg_cap, has_roots, root_dims_,
                     plan_.needs.widest, plan_.needs.max_d, big_points_, plan_.grid_sub, st_);
     ENGINE_TRY(cudaGetLastError());
     root_dims_ = false;

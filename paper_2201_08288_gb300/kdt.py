@@ -403,7 +403,11 @@ class Server:
         self._keep = {}
 
     def submit(self, item, outputs=None) -> int:
+        """Queue a build. The server reads the inputs on its own stream, so the
+        stream that produced them is synchronised first."""
+        import torch
         descs, outs = make_descs([item], [outputs] if outputs is not None else None)
+        torch.cuda.current_stream(item["points"].device).synchronize()
         t = ctypes.c_uint64(0)
         st = self._lib.kdt_server_submit(self._h, descs, ctypes.byref(t))
         if st:
