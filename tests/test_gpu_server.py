@@ -108,3 +108,21 @@ def test_request_larger_than_budget_is_refused_and_unknown_ticket():
         with pytest.raises(kdt.KdtError) as e:
             sv.poll(12345, 0)
         assert e.value.status == 9
+
+
+def test_inputs_drawn_on_the_device_just_before_submit():
+    """Requests whose points are produced by kernels on the caller's stream
+    right before submit (the server reads them on its own stream)."""
+    from paper_2201_08288_gb300 import kdt
+    dev = torch.device("cuda:0")
+    _, specs = workloads.config5_stream(num_requests=24, rate=1000.0, n_lo=11.0, n_hi=16.0, seed=11)
+    with kdt.Server(8 << 30, 64) as sv:
+        items = [dict(points=s.points_device(dev), r=32, subset_mode=0, depth=0, leaf_size=64,
+                      max_levels=s.max_levels, key_rule=0) for s in specs]
+        tickets = [sv.submit(it) for it in items]
+        results = [sv.poll(t) for t in tickets]
+    assert all(r[0] == 0 for r in results)
+    for i in (0, 5, 11, 23):
+        pts = items[i]["points"].cpu().numpy()
+        kw = {k: v for k, v in items[i].items() if k != "points"}
+        assert_same_tree(_host_tree(results[i][1]), oracle.build_tree(pts, **kw), f"req {i}")
