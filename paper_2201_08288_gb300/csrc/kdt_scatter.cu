@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
 
   if (warp == kCW) {
     // ================================================================ producer
-    uint32_t ephase[2] = {0u, 0u};
+    uint32_t ephase = 0u;  // bit b: parity of buffer b's next "empty" phase
     uint32_t k = 0;
     // the next tile's record and cell are loaded one tile ahead
     uint2 tl_next = blockIdx.x < ntiles ? s.tiles[blockIdx.x] : make_uint2(0, 0);
@@ -124,11 +124,11 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       for (uint32_t sub = tl.y; sub < tend; sub += T, ++k) {
         const int b = k & 1;
         if (k >= 2) {
-          if (!mbar_wait_bounded(&empty[b], ephase[b])) {
+          if (!mbar_wait_bounded(&empty[b], (ephase >> b) & 1u)) {
             if (lane == 0) atomicExch(&s_fail, 1u);
             return;
           }
-          ephase[b] ^= 1u;
+          ephase ^= 1u << b;
         }
         if (s_fail) return;
         const uint32_t mcnt = min(T, tend - sub);
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
 
   // ================================================================== consumers
   const unsigned lt_mask = (1u << lane) - 1u;
-  uint32_t fphase[2] = {0u, 0u};
+  uint32_t fphase = 0u;  // bit b: parity of buffer b's next "full" phase
   uint32_t lnext = 0, rnext = 0;
   bool saw_nan = false;
   bool fresh = true;  // tmm holds nothing yet of the current cell
@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     for (bool more = true; more; ++k) {
       const int b = k & 1;
-      if (!mbar_wait_bounded(&full[b], fphase[b])) atomicExch(&s_fail, 1u);
-      fphase[b] ^= 1u;
+      if (!mbar_wait_bounded(&full[b], (fphase >> b) & 1u)) atomicExch(&s_fail, 1u);
+      fphase ^= 1u << b;
       named_sync(kConsumerBar, kCT);
       if (s_fail) return;
       const SubMeta& m = meta[b];

@@ -43,7 +43,7 @@ constexpr uint32_t kRankMax = 32;
 struct Smem {
   uint32_t* whist;    // NW * 256 words: warp histograms, tables of few cells, root subset counts
   uint16_t* biglist;  // kSubtreeBigCap segments above kRankMax points
-  LCell* tab[2];      // kSubtreeSmemCells each
+  LCell* tab;        // 2 * kSubtreeSmemCells: the cell tables of two levels
   uint32_t* cols;     // (d + 1) columns at stride `stride`; column d is the permutation
   uint32_t* gk;       // N: key of each position on its cell's coordinate
   uint32_t* smed;     // N: median of each segment
@@ -67,10 +67,8 @@ __device__ Smem carve(uint8_t* base, uint32_t N, int d) {
   p += (size_t)NW * 256 * 4;
   s.biglist = (uint16_t*)p;
   p += kSubtreeBigCap * 2;
-  s.tab[0] = (LCell*)p;
-  p += kSubtreeSmemCells * sizeof(LCell);
-  s.tab[1] = (LCell*)p;
-  p += kSubtreeSmemCells * sizeof(LCell);
+  s.tab = (LCell*)p;
+  p += 2 * kSubtreeSmemCells * sizeof(LCell);
   const uint32_t stride = subtree_stride(N);
   s.cols = (uint32_t*)p;
   p += (size_t)(d + 1) * stride * 4;
@@ -144,8 +142,10 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
   };
   __shared__ CombineState s_cmb[kSubtreeWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  LCell* gslice[2] = {slices + (size_t)blockIdx.x * 2 * slice_cells,
-                      slices + (size_t)blockIdx.x * 2 * slice_cells + slice_cells};
+  // this CTA's two global cell tables (for levels with too many cells for
+  // shared memory); tables are picked by offset, never by an indexed array,
+  // so that no pointer array of this kernel lives in local memory
+  LCell* const gslice = slices + (size_t)blockIdx.x * 2 * slice_cells;
   if (tid == 0) {
     mbar_init(&s_bar, 1);
     mbar_init_fence();
@@ -264,7 +264,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
         for (uint32_t i = tid; i < N; i += T) S.ordA[i] = (uint16_t)i;
       }
       if (tid == 0) {
-        S.tab[0][0] = LCell{c.heap, 0u, 0, (uint16_t)N, 0, 0, (uint8_t)c.stall};
+        S.tab[0] = LCell{c.heap, 0u, 0, (uint16_t)N, 0, 0, (uint8_t)c.stall};
         s_ncur = 1;
         s_where = 0;
       }
@@ -279,7 +279,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
     for (;;) {
       const uint32_t ncur = s_ncur;
       if (ncur == 0) break;
-      LCell* cc = s_where ? gslice[which] : S.tab[which];
+      LCell* cc = s_where ? gslice + (size_t)which * slice_cells : S.tab + which * kSubtreeSmemCells;
 
       // ---- 1. key coordinate of every live cell
       if (t.key_rule == KEY_CYCLIC) {
@@ -327,8 +327,13 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
                 const uint32_t h = __reduce_max_sync(0xffffffffu, hi[q]);
                 const int col = c0 + q;
                 if (lane == (col & 31)) {
-                  lo2[col >> 5] = l;
-                  hi2[col >> 5] = h;
+                  if (col < 32) {
+                    lo2[0] = l;
+                    hi2[0] = h;
+                  } else {
+                    lo2[1] = l;
+                    hi2[1] = h;
+                  }
                 }
               }
           }
@@ -599,7 +604,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
         block_excl_scan(sum, tmp, &total_live);
       }
       const int nwhere = total_live <= (uint32_t)kSubtreeSmemCells ? 0 : 1;
-      LCell* nc = nwhere ? gslice[which ^ 1] : S.tab[which ^ 1];
+      LCell* nc = nwhere ? gslice + (size_t)(which ^ 1) * slice_cells : S.tab + (which ^ 1) * kSubtreeSmemCells;
       uint32_t run_out = 0;
       for (uint32_t k0 = 0; k0 < ncur; k0 += T) {
         const uint32_t k = k0 + tid;
@@ -611,6 +616,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
           const int stall = (R == 0) ? p.stall + 1 : 0;
           const uint32_t cbeg[2] = {p.begin, p.begin + L};
           const uint32_t cn[2] = {L, R};
+#pragma unroll
           for (int side = 0; side < 2; ++side) {
             const uint32_t heap = 2u * p.heap + 1u + (uint32_t)side;
             if (is_terminal(t, cn[side], nlevel, stall)) {
