@@ -439,9 +439,9 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
           if (lane == 0) cc[k].mkey = m;
         }
       } else {
-        // few cells: G warps per cell, each counting into its own histogram;
-        // the finder of a cell sums its G histograms. Every cell starts at the
-        // first bit where its segment medians differ.
+        // few cells: G warps per cell add into the cell's one 256-bin
+        // histogram; warp k finds cell k's digit and zeroes the bins it read.
+        // Every cell starts at the first bit where its segment medians differ.
         const uint32_t G = (uint32_t)NW / ncur;
         const uint32_t k = warp / G, part = warp % G;
         uint32_t e = 0, s0 = 0, s1 = 0;
@@ -451,6 +451,8 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
           s0 = S.pre[b];
           s1 = S.pre[e];
         }
+        uint32_t* hist = S.whist;  // [ncur][256], ncur < NW
+        for (uint32_t j = tid; j < ncur * 256u; j += T) hist[j] = 0;
         if (tid < ncur) {
           s_cmb[tid].lo = 0xffffffffu;
           s_cmb[tid].hi = 0u;
@@ -482,56 +484,36 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
           uint32_t more = 0;
           for (uint32_t kk = 0; kk < ncur; ++kk) more |= s_cmb[kk].rem;
           if (!more) break;
-          uint32_t rem = 0, prefix = 0, shift = 0, nb = 1, hmask = 0;
           if (k < ncur) {
-            rem = s_cmb[k].rem;
-            prefix = s_cmb[k].prefix;
-            const uint32_t bits = rem < 8u ? rem : 8u;
-            shift = rem - bits;
-            nb = 1u << bits;
-            hmask = rem >= 32u ? 0u : ~((1u << rem) - 1u);
-          }
-          uint32_t* hist = S.whist + warp * 256;
-          for (uint32_t i = lane; i < 256u; i += 32) hist[i] = 0;
-          __syncwarp();
-          if (k < ncur && rem > 0)
-            for (uint32_t j = s0 + part * 32 + lane; j < s1; j += G * 32) {
-              const uint32_t key = S.smed[j];
-              if ((key & hmask) == prefix)
-                atomic_add_shared(&hist[(key >> shift) & (nb - 1u)], min((uint32_t)S.segs[j + 1], e) - S.segs[j]);
-            }
-          __syncthreads();
-          if (k < ncur && part == 0 && rem > 0) {
-            // sum the cell's G histograms while finding the digit
-            const uint32_t per = nb >= 32u ? nb / 32u : 1u;
-            const uint32_t first = lane * per;
-            uint32_t local[8];
-            uint32_t sum = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              uint32_t v = 0;
-              if ((uint32_t)q < per && first + q < nb)
-                for (uint32_t g = 0; g < G; ++g) v += hist[g * 256u + first + q];
-              local[q] = v;
-              sum += v;
-            }
-            const uint32_t rank = s_cmb[k].rank;
-            const uint32_t incl = warp_incl_scan(sum), excl = incl - sum;
-            const unsigned bal = __ballot_sync(0xffffffffu, rank >= excl && rank < incl);
-            const int owner = bal ? __ffs(bal) - 1 : 31;
-            if (lane == owner) {
-              uint32_t acc = excl, digit = 0;
-#pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                if ((uint32_t)q < per && rank < acc + local[q]) {
-                  digit = first + q;
-                  break;
-                }
-                acc += local[q];
+            const uint32_t rem = s_cmb[k].rem, prefix = s_cmb[k].prefix;
+            if (rem > 0) {
+              const uint32_t bits = rem < 8u ? rem : 8u;
+              const uint32_t shift = rem - bits, nb = 1u << bits;
+              const uint32_t hmask = rem >= 32u ? 0u : ~((1u << rem) - 1u);
+              uint32_t* h = hist + k * 256u;
+              for (uint32_t j = s0 + part * 32 + lane; j < s1; j += G * 32) {
+                const uint32_t key = S.smed[j];
+                if ((key & hmask) == prefix)
+                  atomic_add_shared(&h[(key >> shift) & (nb - 1u)], min((uint32_t)S.segs[j + 1], e) - S.segs[j]);
               }
-              s_cmb[k].rank = rank - acc;
-              s_cmb[k].prefix = prefix | (digit << shift);
-              s_cmb[k].rem = shift;
+            }
+          }
+          __syncthreads();
+          if ((uint32_t)warp < ncur) {
+            const uint32_t rem = s_cmb[warp].rem;
+            if (rem > 0) {
+              const uint32_t bits = rem < 8u ? rem : 8u;
+              const uint32_t shift = rem - bits, nb = 1u << bits;
+              uint32_t* h = hist + warp * 256u;
+              uint32_t below;
+              const uint32_t digit = warp_find_digit_n(h, nb, s_cmb[warp].rank, &below);
+              __syncwarp();  // every lane has read its bins
+              for (uint32_t i = lane; i < nb; i += 32) h[i] = 0;  // ready for the next pass
+              if (lane == 0) {
+                s_cmb[warp].rank -= below;
+                s_cmb[warp].prefix |= digit << shift;
+                s_cmb[warp].rem = shift;
+              }
             }
           }
           __syncthreads();
