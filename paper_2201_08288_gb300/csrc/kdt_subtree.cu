@@ -23,6 +23,7 @@
 // The permutation is written once, at the end. The kernel is persistent: each
 // CTA pulls cells from a queue.
 #include <algorithm>
+#include <type_traits>
 
 #include "kdt_internal.cuh"
 #include "kdt_launch.h"
@@ -279,364 +280,374 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
     for (;;) {
       const uint32_t ncur = s_ncur;
       if (ncur == 0) break;
-      LCell* cc = s_where ? gslice + (size_t)which * slice_cells : S.tab + which * kSubtreeSmemCells;
+      // The body of a level is compiled twice: for a cell table in shared
+      // memory (the usual case, accessed with shared-memory loads) and for one
+      // that outgrew it and lives in this CTA's global slice.
+      auto level_body = [&](auto in_global) {
+        LCell* cc = decltype(in_global)::value ? gslice + (size_t)which * slice_cells
+                                               : S.tab + which * kSubtreeSmemCells;
 
-      // ---- 1. key coordinate of every live cell
-      if (t.key_rule == KEY_CYCLIC) {
-        for (uint32_t k = tid; k < ncur; k += T) cc[k].dim = (uint8_t)(level % d);
-      } else {
-        // per (cell, part): min and max key of every coordinate, coordinate l
-        // ending in lane l % 32; G warps share a cell when there are few cells
-        const uint32_t G = ncur >= (uint32_t)NW ? 1u : (uint32_t)NW / ncur;
-        uint32_t* tab = S.whist;  // few cells: [ncur][d][2]
-        if (G > 1) {
-          for (uint32_t j = tid; j < ncur * (uint32_t)d; j += T) {
-            tab[2 * j] = 0xffffffffu;
-            tab[2 * j + 1] = 0u;
-          }
-          __syncthreads();
-        }
-        for (uint32_t w0 = warp; w0 < ncur * G; w0 += NW) {
-          const uint32_t k = w0 / G, part = w0 % G;
-          const uint32_t b = cc[k].begin, cnt = cc[k].count;
-          const uint32_t i0 = b + (cnt * part) / G, i1 = b + (cnt * (part + 1)) / G;
-          uint32_t lo2[2] = {0xffffffffu, 0xffffffffu}, hi2[2] = {0u, 0u};
-          for (int c0 = 0; c0 < d; c0 += 8) {
-            const int nc = min(8, d - c0);
-            uint32_t base[8], lo[8], hi[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              base[q] = q < nc ? s_colbase[c0 + q] : 0u;
-              lo[q] = 0xffffffffu;
-              hi[q] = 0u;
+        // ---- 1. key coordinate of every live cell
+        if (t.key_rule == KEY_CYCLIC) {
+          for (uint32_t k = tid; k < ncur; k += T) cc[k].dim = (uint8_t)(level % d);
+        } else {
+          // per (cell, part): min and max key of every coordinate, coordinate l
+          // ending in lane l % 32; G warps share a cell when there are few cells
+          const uint32_t G = ncur >= (uint32_t)NW ? 1u : (uint32_t)NW / ncur;
+          uint32_t* tab = S.whist;  // few cells: [ncur][d][2]
+          if (G > 1) {
+            for (uint32_t j = tid; j < ncur * (uint32_t)d; j += T) {
+              tab[2 * j] = 0xffffffffu;
+              tab[2 * j + 1] = 0u;
             }
-            for (uint32_t i = i0 + lane; i < i1; i += 32) {
-              const uint32_t o = ordA[i];
-#pragma unroll
+            __syncthreads();
+          }
+          for (uint32_t w0 = warp; w0 < ncur * G; w0 += NW) {
+            const uint32_t k = w0 / G, part = w0 % G;
+            const uint32_t b = cc[k].begin, cnt = cc[k].count;
+            const uint32_t i0 = b + (cnt * part) / G, i1 = b + (cnt * (part + 1)) / G;
+            uint32_t lo2[2] = {0xffffffffu, 0xffffffffu}, hi2[2] = {0u, 0u};
+            for (int c0 = 0; c0 < d; c0 += 8) {
+              const int nc = min(8, d - c0);
+              uint32_t base[8], lo[8], hi[8];
+  #pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                base[q] = q < nc ? s_colbase[c0 + q] : 0u;
+                lo[q] = 0xffffffffu;
+                hi[q] = 0u;
+              }
+              for (uint32_t i = i0 + lane; i < i1; i += 32) {
+                const uint32_t o = ordA[i];
+  #pragma unroll
+                for (int q = 0; q < 8; ++q)
+                  if (q < nc) {
+                    const uint32_t kk = S.cols[base[q] + o];
+                    lo[q] = min(lo[q], kk);
+                    hi[q] = max(hi[q], kk);
+                  }
+              }
+  #pragma unroll
               for (int q = 0; q < 8; ++q)
                 if (q < nc) {
-                  const uint32_t kk = S.cols[base[q] + o];
-                  lo[q] = min(lo[q], kk);
-                  hi[q] = max(hi[q], kk);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-              if (q < nc) {
-                const uint32_t l = __reduce_min_sync(0xffffffffu, lo[q]);
-                const uint32_t h = __reduce_max_sync(0xffffffffu, hi[q]);
-                const int col = c0 + q;
-                if (lane == (col & 31)) {
-                  if (col < 32) {
-                    lo2[0] = l;
-                    hi2[0] = h;
-                  } else {
-                    lo2[1] = l;
-                    hi2[1] = h;
+                  const uint32_t l = __reduce_min_sync(0xffffffffu, lo[q]);
+                  const uint32_t h = __reduce_max_sync(0xffffffffu, hi[q]);
+                  const int col = c0 + q;
+                  if (lane == (col & 31)) {
+                    if (col < 32) {
+                      lo2[0] = l;
+                      hi2[0] = h;
+                    } else {
+                      lo2[1] = l;
+                      hi2[1] = h;
+                    }
                   }
                 }
-              }
-          }
-          if (G == 1) {
-            const int best = warp_pick_widest(lo2, hi2, d);
-            if (lane == 0) cc[k].dim = (uint8_t)best;
-          } else {
-            for (int h2 = 0; h2 < 2; ++h2) {
-              const int col = lane + 32 * h2;
-              if (col < d) {
-                atomic_min_shared(&tab[(k * d + col) * 2], lo2[h2]);
-                atomic_max_shared(&tab[(k * d + col) * 2 + 1], hi2[h2]);
-              }
             }
-          }
-        }
-        if (G > 1) {
-          __syncthreads();
-          for (uint32_t k = warp; k < ncur; k += NW) {
-            uint32_t lo2[2], hi2[2];
-            for (int h2 = 0; h2 < 2; ++h2) {
-              const int col = lane + 32 * h2;
-              lo2[h2] = col < d ? tab[(k * d + col) * 2] : 0u;
-              hi2[h2] = col < d ? tab[(k * d + col) * 2 + 1] : 0u;
-            }
-            const int best = warp_pick_widest(lo2, hi2, d);
-            if (lane == 0) cc[k].dim = (uint8_t)best;
-          }
-        }
-      }
-      __syncthreads();
-
-      // ---- 2. keys in local order, segment starts, their numbering
-      for (uint32_t i = tid; i < N; i += T) {
-        const uint16_t k = S.cellid[i];
-        uint16_t f = 0;
-        if (k != kNoCell) {
-          const uint32_t o = ordA[i];
-          S.gk[i] = S.cols[s_colbase[cc[k].dim] + o];
-          f = (i == cc[k].begin) || S.sid[o] != S.sid[ordA[i - 1]];
-        }
-        S.aux[i] = f;
-      }
-      if (tid == 0) s_nbig = 0;
-      __syncthreads();
-      scan_flags(S.aux, S.pre, N, tmp);
-      __syncthreads();
-      const uint32_t nseg = S.pre[N];
-      for (uint32_t i = tid; i < N; i += T)
-        if (S.aux[i]) S.segs[S.pre[i]] = (uint16_t)i;
-      if (tid == 0) S.segs[nseg] = (uint16_t)N;
-      __syncthreads();
-
-      // ---- 3. lower median of every segment
-      for (uint32_t i = tid; i < N; i += T) {
-        const uint16_t k = S.cellid[i];
-        if (k == kNoCell) continue;
-        const uint32_t sx = (uint32_t)S.pre[i] + S.aux[i] - 1u;
-        const uint32_t b = S.segs[sx], e = min((uint32_t)S.segs[sx + 1], (uint32_t)cc[k].begin + cc[k].count);
-        const uint32_t w = e - b;
-        if (w > kRankMax) {
-          if (i == b) {
-            const uint32_t slot = atomicAdd(&s_nbig, 1u);
-            if (slot < (uint32_t)kSubtreeBigCap) S.biglist[slot] = (uint16_t)sx; else set_status(t, ST_INTERNAL);
-          }
-          continue;
-        }
-        const uint32_t key = S.gk[i];
-        uint32_t rk = 0;
-        for (uint32_t j = b; j < e; ++j) {
-          const uint32_t kj = S.gk[j];
-          rk += (kj < key) | ((kj == key) & (j < i));
-        }
-        if (rk == (w - 1) / 2) S.smed[sx] = key;
-      }
-      __syncthreads();
-      {
-        const uint32_t nbig = min(s_nbig, (uint32_t)kSubtreeBigCap);
-        for (uint32_t j = warp; j < nbig; j += NW) {
-          const uint32_t sx = S.biglist[j];
-          const uint32_t b = S.segs[sx];
-          const uint16_t k = S.cellid[b];
-          const uint32_t e = min((uint32_t)S.segs[sx + 1], (uint32_t)cc[k].begin + cc[k].count);
-          const uint32_t* g = S.gk + b;
-          const uint32_t m = warp_weighted_select<true>(e - b, (e - b - 1) / 2, S.whist + warp * 256,
-                                                        [&](uint32_t jj) { return g[jj]; },
-                                                        [](uint32_t) { return 1u; });
-          if (lane == 0) S.smed[sx] = m;
-        }
-      }
-      __syncthreads();
-
-      // ---- 4. weighted lower median per cell: the smallest segment median m
-      // whose segments with median <= m hold >= ceil(W/2) points, i.e. the
-      // key of weighted rank (W-1)/2. A cell's segments are [pre[begin], pre[end]).
-      if (ncur >= (uint32_t)NW) {  // many cells: a warp per cell
-        for (uint32_t k = warp; k < ncur; k += NW) {
-          const uint32_t b = cc[k].begin, e = b + cc[k].count;
-          const uint32_t s0 = S.pre[b], s1 = S.pre[e];
-          const uint32_t m = warp_weighted_select(
-              s1 - s0, (cc[k].count - 1u) / 2u, S.whist + warp * 256, [&](uint32_t j) { return S.smed[s0 + j]; },
-              [&](uint32_t j) { return min((uint32_t)S.segs[s0 + j + 1], e) - S.segs[s0 + j]; });
-          if (lane == 0) cc[k].mkey = m;
-        }
-      } else {
-        // few cells: G warps per cell add into the cell's one 256-bin
-        // histogram; warp k finds cell k's digit and zeroes the bins it read.
-        // Every cell starts at the first bit where its segment medians differ.
-        const uint32_t G = (uint32_t)NW / ncur;
-        const uint32_t k = warp / G, part = warp % G;
-        uint32_t e = 0, s0 = 0, s1 = 0;
-        if (k < ncur) {
-          const uint32_t b = cc[k].begin;
-          e = b + cc[k].count;
-          s0 = S.pre[b];
-          s1 = S.pre[e];
-        }
-        uint32_t* hist = S.whist;  // [ncur][256], ncur < NW
-        for (uint32_t j = tid; j < ncur * 256u; j += T) hist[j] = 0;
-        if (tid < ncur) {
-          s_cmb[tid].lo = 0xffffffffu;
-          s_cmb[tid].hi = 0u;
-        }
-        __syncthreads();
-        if (k < ncur) {
-          uint32_t lo = 0xffffffffu, hi = 0u;
-          for (uint32_t j = s0 + part * 32 + lane; j < s1; j += G * 32) {
-            lo = min(lo, S.smed[j]);
-            hi = max(hi, S.smed[j]);
-          }
-          lo = __reduce_min_sync(0xffffffffu, lo);
-          hi = __reduce_max_sync(0xffffffffu, hi);
-          if (lane == 0) {
-            atomic_min_shared(&s_cmb[k].lo, lo);
-            atomic_max_shared(&s_cmb[k].hi, hi);
-          }
-        }
-        __syncthreads();
-        if (tid < ncur) {
-          const uint32_t lo = s_cmb[tid].lo, hi = s_cmb[tid].hi;
-          const int rem = lo >= hi ? 0 : 32 - __clz(lo ^ hi);
-          s_cmb[tid].rem = (uint32_t)rem;
-          s_cmb[tid].prefix = rem == 0 ? lo : (rem == 32 ? 0u : (lo & ~((1u << rem) - 1u)));
-          s_cmb[tid].rank = (cc[tid].count - 1u) / 2u;
-        }
-        __syncthreads();
-        for (;;) {
-          uint32_t more = 0;
-          for (uint32_t kk = 0; kk < ncur; ++kk) more |= s_cmb[kk].rem;
-          if (!more) break;
-          if (k < ncur) {
-            const uint32_t rem = s_cmb[k].rem, prefix = s_cmb[k].prefix;
-            if (rem > 0) {
-              const uint32_t bits = rem < 8u ? rem : 8u;
-              const uint32_t shift = rem - bits, nb = 1u << bits;
-              const uint32_t hmask = rem >= 32u ? 0u : ~((1u << rem) - 1u);
-              uint32_t* h = hist + k * 256u;
-              for (uint32_t j = s0 + part * 32 + lane; j < s1; j += G * 32) {
-                const uint32_t key = S.smed[j];
-                if ((key & hmask) == prefix)
-                  atomic_add_shared(&h[(key >> shift) & (nb - 1u)], min((uint32_t)S.segs[j + 1], e) - S.segs[j]);
-              }
-            }
-          }
-          __syncthreads();
-          if ((uint32_t)warp < ncur) {
-            const uint32_t rem = s_cmb[warp].rem;
-            if (rem > 0) {
-              const uint32_t bits = rem < 8u ? rem : 8u;
-              const uint32_t shift = rem - bits, nb = 1u << bits;
-              uint32_t* h = hist + warp * 256u;
-              uint32_t below;
-              const uint32_t digit = warp_find_digit_n(h, nb, s_cmb[warp].rank, &below);
-              __syncwarp();  // every lane has read its bins
-              for (uint32_t i = lane; i < nb; i += 32) h[i] = 0;  // ready for the next pass
-              if (lane == 0) {
-                s_cmb[warp].rank -= below;
-                s_cmb[warp].prefix |= digit << shift;
-                s_cmb[warp].rem = shift;
-              }
-            }
-          }
-          __syncthreads();
-        }
-        if (tid < ncur) cc[tid].mkey = s_cmb[tid].prefix;
-      }
-      __syncthreads();
-      for (uint32_t k = tid; k < ncur; k += T) {
-        t.out_vals[cc[k].heap] = key_float(cc[k].mkey);
-        t.out_dims[cc[k].heap] = (int8_t)cc[k].dim;
-      }
-
-      // ---- 5. stable partition of the local order (key <= split to the left);
-      // the left flags are formed inside the scan
-      {
-        const uint32_t per = (N + T - 1) / T;
-        const uint32_t q0 = min(N, tid * per), q1 = min(N, q0 + per);
-        uint32_t sum = 0;
-        for (uint32_t q = q0; q < q1; ++q) {
-          const uint16_t k = S.cellid[q];
-          const uint16_t f = (k != kNoCell) && S.gk[q] <= cc[k].mkey;
-          S.aux[q] = f;
-          sum += f;
-        }
-        uint32_t tot;
-        uint32_t run = block_excl_scan(sum, tmp, &tot);
-        for (uint32_t q = q0; q < q1; ++q) {
-          S.pre[q] = (uint16_t)run;
-          run += S.aux[q];
-        }
-        if (tid == 0) S.pre[N] = (uint16_t)tot;
-      }
-      __syncthreads();
-      for (uint32_t k = tid; k < ncur; k += T)
-        cc[k].lcount = (uint16_t)(S.pre[cc[k].begin + cc[k].count] - S.pre[cc[k].begin]);
-      for (uint32_t i = tid; i < N; i += T) {
-        const uint16_t k = S.cellid[i];
-        if (k == kNoCell) {
-          ordB[i] = ordA[i];
-          continue;
-        }
-        const uint32_t b = cc[k].begin;
-        const uint32_t lb = (uint32_t)S.pre[i] - S.pre[b];
-        const uint32_t L = (uint32_t)S.pre[b + cc[k].count] - S.pre[b];
-        const uint32_t dst = S.aux[i] ? b + lb : b + L + (i - b - lb);
-        ordB[dst] = ordA[i];
-      }
-      __syncthreads();
-      {
-        uint16_t* x = ordA;
-        ordA = ordB;
-        ordB = x;
-      }
-
-      // ---- 6. children: one scan over the cells numbers the live children
-      // (their number is parked in the parent's mkey); then every position
-      // takes its child's number
-      const int nlevel = level + 1;
-      uint32_t total_live = 0;
-      {
-        // count the live children first to choose where the next table lives
-        uint32_t sum = 0;
-        for (uint32_t k = tid; k < ncur; k += T) {
-          const LCell p = cc[k];
-          const uint32_t L = p.lcount, R = p.count - L;
-          const int stall = (R == 0) ? p.stall + 1 : 0;
-          const bool cap = t.depth == 0 && nlevel >= t.max_levels;
-          sum += (!is_terminal(t, L, nlevel, stall) && !cap) + (!is_terminal(t, R, nlevel, stall) && !cap);
-        }
-        block_excl_scan(sum, tmp, &total_live);
-      }
-      const int nwhere = total_live <= (uint32_t)kSubtreeSmemCells ? 0 : 1;
-      LCell* nc = nwhere ? gslice + (size_t)(which ^ 1) * slice_cells : S.tab + (which ^ 1) * kSubtreeSmemCells;
-      uint32_t run_out = 0;
-      for (uint32_t k0 = 0; k0 < ncur; k0 += T) {
-        const uint32_t k = k0 + tid;
-        LCell ch[2] = {};
-        bool live[2] = {false, false};
-        if (k < ncur) {
-          const LCell p = cc[k];
-          const uint32_t L = p.lcount, R = p.count - L;
-          const int stall = (R == 0) ? p.stall + 1 : 0;
-          const uint32_t cbeg[2] = {p.begin, p.begin + L};
-          const uint32_t cn[2] = {L, R};
-#pragma unroll
-          for (int side = 0; side < 2; ++side) {
-            const uint32_t heap = 2u * p.heap + 1u + (uint32_t)side;
-            if (is_terminal(t, cn[side], nlevel, stall)) {
-              record_terminal(t, c.begin + cbeg[side], cn[side], heap, nlevel);
-            } else if (t.depth == 0 && nlevel >= t.max_levels) {
-              set_status(t, ST_LEVEL_CAP);
+            if (G == 1) {
+              const int best = warp_pick_widest(lo2, hi2, d);
+              if (lane == 0) cc[k].dim = (uint8_t)best;
             } else {
-              ch[side] = LCell{heap, 0u, (uint16_t)cbeg[side], (uint16_t)cn[side], 0, 0, (uint8_t)stall};
-              live[side] = true;
+              for (int h2 = 0; h2 < 2; ++h2) {
+                const int col = lane + 32 * h2;
+                if (col < d) {
+                  atomic_min_shared(&tab[(k * d + col) * 2], lo2[h2]);
+                  atomic_max_shared(&tab[(k * d + col) * 2 + 1], hi2[h2]);
+                }
+              }
+            }
+          }
+          if (G > 1) {
+            __syncthreads();
+            for (uint32_t k = warp; k < ncur; k += NW) {
+              uint32_t lo2[2], hi2[2];
+              for (int h2 = 0; h2 < 2; ++h2) {
+                const int col = lane + 32 * h2;
+                lo2[h2] = col < d ? tab[(k * d + col) * 2] : 0u;
+                hi2[h2] = col < d ? tab[(k * d + col) * 2 + 1] : 0u;
+              }
+              const int best = warp_pick_widest(lo2, hi2, d);
+              if (lane == 0) cc[k].dim = (uint8_t)best;
             }
           }
         }
-        const uint32_t nlive = (uint32_t)live[0] + (uint32_t)live[1];
-        uint32_t tot;
-        const uint32_t ex = block_excl_scan(nlive, tmp, &tot);
-        if (k < ncur) {
-          const uint32_t li = live[0] ? run_out + ex : kNoCell;
-          const uint32_t ri = live[1] ? run_out + ex + (live[0] ? 1u : 0u) : kNoCell;
-          if (live[0]) nc[li] = ch[0];
-          if (live[1]) nc[ri] = ch[1];
-          cc[k].mkey = li | (ri << 16);
+        __syncthreads();
+
+        // ---- 2. keys in local order, segment starts, their numbering
+        for (uint32_t i = tid; i < N; i += T) {
+          const uint16_t k = S.cellid[i];
+          uint16_t f = 0;
+          if (k != kNoCell) {
+            const uint32_t o = ordA[i];
+            S.gk[i] = S.cols[s_colbase[cc[k].dim] + o];
+            f = (i == cc[k].begin) || S.sid[o] != S.sid[ordA[i - 1]];
+          }
+          S.aux[i] = f;
         }
-        run_out += tot;
-      }
-      if (tid == 0) {
-        s_ncur = run_out;
-        s_where = (uint32_t)nwhere;
-      }
-      __syncthreads();
-      for (uint32_t i = tid; i < N; i += T) {
-        const uint16_t k = S.cellid[i];
-        if (k == kNoCell) continue;
-        const uint32_t side = (i - cc[k].begin) >= cc[k].lcount ? 16u : 0u;
-        S.cellid[i] = (uint16_t)(cc[k].mkey >> side);
-      }
-      __syncthreads();
-      which ^= 1;
-      level = nlevel;
+        if (tid == 0) s_nbig = 0;
+        __syncthreads();
+        scan_flags(S.aux, S.pre, N, tmp);
+        __syncthreads();
+        const uint32_t nseg = S.pre[N];
+        for (uint32_t i = tid; i < N; i += T)
+          if (S.aux[i]) S.segs[S.pre[i]] = (uint16_t)i;
+        if (tid == 0) S.segs[nseg] = (uint16_t)N;
+        __syncthreads();
+
+        // ---- 3. lower median of every segment
+        for (uint32_t i = tid; i < N; i += T) {
+          const uint16_t k = S.cellid[i];
+          if (k == kNoCell) continue;
+          const uint32_t sx = (uint32_t)S.pre[i] + S.aux[i] - 1u;
+          const uint32_t b = S.segs[sx], e = min((uint32_t)S.segs[sx + 1], (uint32_t)cc[k].begin + cc[k].count);
+          const uint32_t w = e - b;
+          if (w > kRankMax) {
+            if (i == b) {
+              const uint32_t slot = atomicAdd(&s_nbig, 1u);
+              if (slot < (uint32_t)kSubtreeBigCap) S.biglist[slot] = (uint16_t)sx; else set_status(t, ST_INTERNAL);
+            }
+            continue;
+          }
+          const uint32_t key = S.gk[i];
+          uint32_t rk = 0;
+          for (uint32_t j = b; j < e; ++j) {
+            const uint32_t kj = S.gk[j];
+            rk += (kj < key) | ((kj == key) & (j < i));
+          }
+          if (rk == (w - 1) / 2) S.smed[sx] = key;
+        }
+        __syncthreads();
+        {
+          const uint32_t nbig = min(s_nbig, (uint32_t)kSubtreeBigCap);
+          for (uint32_t j = warp; j < nbig; j += NW) {
+            const uint32_t sx = S.biglist[j];
+            const uint32_t b = S.segs[sx];
+            const uint16_t k = S.cellid[b];
+            const uint32_t e = min((uint32_t)S.segs[sx + 1], (uint32_t)cc[k].begin + cc[k].count);
+            const uint32_t* g = S.gk + b;
+            const uint32_t m = warp_weighted_select<true>(e - b, (e - b - 1) / 2, S.whist + warp * 256,
+                                                          [&](uint32_t jj) { return g[jj]; },
+                                                          [](uint32_t) { return 1u; });
+            if (lane == 0) S.smed[sx] = m;
+          }
+        }
+        __syncthreads();
+
+        // ---- 4. weighted lower median per cell: the smallest segment median m
+        // whose segments with median <= m hold >= ceil(W/2) points, i.e. the
+        // key of weighted rank (W-1)/2. A cell's segments are [pre[begin], pre[end]).
+        if (ncur >= (uint32_t)NW) {  // many cells: a warp per cell
+          for (uint32_t k = warp; k < ncur; k += NW) {
+            const uint32_t b = cc[k].begin, e = b + cc[k].count;
+            const uint32_t s0 = S.pre[b], s1 = S.pre[e];
+            const uint32_t m = warp_weighted_select(
+                s1 - s0, (cc[k].count - 1u) / 2u, S.whist + warp * 256, [&](uint32_t j) { return S.smed[s0 + j]; },
+                [&](uint32_t j) { return min((uint32_t)S.segs[s0 + j + 1], e) - S.segs[s0 + j]; });
+            if (lane == 0) cc[k].mkey = m;
+          }
+        } else {
+          // few cells: G warps per cell add into the cell's one 256-bin
+          // histogram; warp k finds cell k's digit and zeroes the bins it read.
+          // Every cell starts at the first bit where its segment medians differ.
+          const uint32_t G = (uint32_t)NW / ncur;
+          const uint32_t k = warp / G, part = warp % G;
+          uint32_t e = 0, s0 = 0, s1 = 0;
+          if (k < ncur) {
+            const uint32_t b = cc[k].begin;
+            e = b + cc[k].count;
+            s0 = S.pre[b];
+            s1 = S.pre[e];
+          }
+          uint32_t* hist = S.whist;  // [ncur][256], ncur < NW
+          for (uint32_t j = tid; j < ncur * 256u; j += T) hist[j] = 0;
+          if (tid < ncur) {
+            s_cmb[tid].lo = 0xffffffffu;
+            s_cmb[tid].hi = 0u;
+          }
+          __syncthreads();
+          if (k < ncur) {
+            uint32_t lo = 0xffffffffu, hi = 0u;
+            for (uint32_t j = s0 + part * 32 + lane; j < s1; j += G * 32) {
+              lo = min(lo, S.smed[j]);
+              hi = max(hi, S.smed[j]);
+            }
+            lo = __reduce_min_sync(0xffffffffu, lo);
+            hi = __reduce_max_sync(0xffffffffu, hi);
+            if (lane == 0) {
+              atomic_min_shared(&s_cmb[k].lo, lo);
+              atomic_max_shared(&s_cmb[k].hi, hi);
+            }
+          }
+          __syncthreads();
+          if (tid < ncur) {
+            const uint32_t lo = s_cmb[tid].lo, hi = s_cmb[tid].hi;
+            const int rem = lo >= hi ? 0 : 32 - __clz(lo ^ hi);
+            s_cmb[tid].rem = (uint32_t)rem;
+            s_cmb[tid].prefix = rem == 0 ? lo : (rem == 32 ? 0u : (lo & ~((1u << rem) - 1u)));
+            s_cmb[tid].rank = (cc[tid].count - 1u) / 2u;
+          }
+          __syncthreads();
+          for (;;) {
+            uint32_t more = 0;
+            for (uint32_t kk = 0; kk < ncur; ++kk) more |= s_cmb[kk].rem;
+            if (!more) break;
+            if (k < ncur) {
+              const uint32_t rem = s_cmb[k].rem, prefix = s_cmb[k].prefix;
+              if (rem > 0) {
+                const uint32_t bits = rem < 8u ? rem : 8u;
+                const uint32_t shift = rem - bits, nb = 1u << bits;
+                const uint32_t hmask = rem >= 32u ? 0u : ~((1u << rem) - 1u);
+                uint32_t* h = hist + k * 256u;
+                for (uint32_t j = s0 + part * 32 + lane; j < s1; j += G * 32) {
+                  const uint32_t key = S.smed[j];
+                  if ((key & hmask) == prefix)
+                    atomic_add_shared(&h[(key >> shift) & (nb - 1u)], min((uint32_t)S.segs[j + 1], e) - S.segs[j]);
+                }
+              }
+            }
+            __syncthreads();
+            if ((uint32_t)warp < ncur) {
+              const uint32_t rem = s_cmb[warp].rem;
+              if (rem > 0) {
+                const uint32_t bits = rem < 8u ? rem : 8u;
+                const uint32_t shift = rem - bits, nb = 1u << bits;
+                uint32_t* h = hist + warp * 256u;
+                uint32_t below;
+                const uint32_t digit = warp_find_digit_n(h, nb, s_cmb[warp].rank, &below);
+                __syncwarp();  // every lane has read its bins
+                for (uint32_t i = lane; i < nb; i += 32) h[i] = 0;  // ready for the next pass
+                if (lane == 0) {
+                  s_cmb[warp].rank -= below;
+                  s_cmb[warp].prefix |= digit << shift;
+                  s_cmb[warp].rem = shift;
+                }
+              }
+            }
+            __syncthreads();
+          }
+          if (tid < ncur) cc[tid].mkey = s_cmb[tid].prefix;
+        }
+        __syncthreads();
+        for (uint32_t k = tid; k < ncur; k += T) {
+          t.out_vals[cc[k].heap] = key_float(cc[k].mkey);
+          t.out_dims[cc[k].heap] = (int8_t)cc[k].dim;
+        }
+
+        // ---- 5. stable partition of the local order (key <= split to the left);
+        // the left flags are formed inside the scan
+        {
+          const uint32_t per = (N + T - 1) / T;
+          const uint32_t q0 = min(N, tid * per), q1 = min(N, q0 + per);
+          uint32_t sum = 0;
+          for (uint32_t q = q0; q < q1; ++q) {
+            const uint16_t k = S.cellid[q];
+            const uint16_t f = (k != kNoCell) && S.gk[q] <= cc[k].mkey;
+            S.aux[q] = f;
+            sum += f;
+          }
+          uint32_t tot;
+          uint32_t run = block_excl_scan(sum, tmp, &tot);
+          for (uint32_t q = q0; q < q1; ++q) {
+            S.pre[q] = (uint16_t)run;
+            run += S.aux[q];
+          }
+          if (tid == 0) S.pre[N] = (uint16_t)tot;
+        }
+        __syncthreads();
+        for (uint32_t k = tid; k < ncur; k += T)
+          cc[k].lcount = (uint16_t)(S.pre[cc[k].begin + cc[k].count] - S.pre[cc[k].begin]);
+        for (uint32_t i = tid; i < N; i += T) {
+          const uint16_t k = S.cellid[i];
+          if (k == kNoCell) {
+            ordB[i] = ordA[i];
+            continue;
+          }
+          const uint32_t b = cc[k].begin;
+          const uint32_t lb = (uint32_t)S.pre[i] - S.pre[b];
+          const uint32_t L = (uint32_t)S.pre[b + cc[k].count] - S.pre[b];
+          const uint32_t dst = S.aux[i] ? b + lb : b + L + (i - b - lb);
+          ordB[dst] = ordA[i];
+        }
+        __syncthreads();
+        {
+          uint16_t* x = ordA;
+          ordA = ordB;
+          ordB = x;
+        }
+
+        // ---- 6. children: one scan over the cells numbers the live children
+        // (their number is parked in the parent's mkey); then every position
+        // takes its child's number
+        const int nlevel = level + 1;
+        uint32_t total_live = 0;
+        {
+          // count the live children first to choose where the next table lives
+          uint32_t sum = 0;
+          for (uint32_t k = tid; k < ncur; k += T) {
+            const LCell p = cc[k];
+            const uint32_t L = p.lcount, R = p.count - L;
+            const int stall = (R == 0) ? p.stall + 1 : 0;
+            const bool cap = t.depth == 0 && nlevel >= t.max_levels;
+            sum += (!is_terminal(t, L, nlevel, stall) && !cap) + (!is_terminal(t, R, nlevel, stall) && !cap);
+          }
+          block_excl_scan(sum, tmp, &total_live);
+        }
+        const int nwhere = total_live <= (uint32_t)kSubtreeSmemCells ? 0 : 1;
+        LCell* nc = nwhere ? gslice + (size_t)(which ^ 1) * slice_cells : S.tab + (which ^ 1) * kSubtreeSmemCells;
+        uint32_t run_out = 0;
+        for (uint32_t k0 = 0; k0 < ncur; k0 += T) {
+          const uint32_t k = k0 + tid;
+          LCell ch[2] = {};
+          bool live[2] = {false, false};
+          if (k < ncur) {
+            const LCell p = cc[k];
+            const uint32_t L = p.lcount, R = p.count - L;
+            const int stall = (R == 0) ? p.stall + 1 : 0;
+            const uint32_t cbeg[2] = {p.begin, p.begin + L};
+            const uint32_t cn[2] = {L, R};
+  #pragma unroll
+            for (int side = 0; side < 2; ++side) {
+              const uint32_t heap = 2u * p.heap + 1u + (uint32_t)side;
+              if (is_terminal(t, cn[side], nlevel, stall)) {
+                record_terminal(t, c.begin + cbeg[side], cn[side], heap, nlevel);
+              } else if (t.depth == 0 && nlevel >= t.max_levels) {
+                set_status(t, ST_LEVEL_CAP);
+              } else {
+                ch[side] = LCell{heap, 0u, (uint16_t)cbeg[side], (uint16_t)cn[side], 0, 0, (uint8_t)stall};
+                live[side] = true;
+              }
+            }
+          }
+          const uint32_t nlive = (uint32_t)live[0] + (uint32_t)live[1];
+          uint32_t tot;
+          const uint32_t ex = block_excl_scan(nlive, tmp, &tot);
+          if (k < ncur) {
+            const uint32_t li = live[0] ? run_out + ex : kNoCell;
+            const uint32_t ri = live[1] ? run_out + ex + (live[0] ? 1u : 0u) : kNoCell;
+            if (live[0]) nc[li] = ch[0];
+            if (live[1]) nc[ri] = ch[1];
+            cc[k].mkey = li | (ri << 16);
+          }
+          run_out += tot;
+        }
+        if (tid == 0) {
+          s_ncur = run_out;
+          s_where = (uint32_t)nwhere;
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < N; i += T) {
+          const uint16_t k = S.cellid[i];
+          if (k == kNoCell) continue;
+          const uint32_t side = (i - cc[k].begin) >= cc[k].lcount ? 16u : 0u;
+          S.cellid[i] = (uint16_t)(cc[k].mkey >> side);
+        }
+        __syncthreads();
+        which ^= 1;
+        level = nlevel;
+      };
+      if (s_where)
+        level_body(std::true_type{});
+      else
+        level_body(std::false_type{});
     }
 
     // ---- write the permutation in final order

@@ -96,6 +96,20 @@ def test_dims_around_subtree_capacity(d):
         check_against_oracle(pts, r=5, subset_mode=0, depth=6, key_rule=d % 2)
 
 
+@pytest.mark.parametrize("d", [1, 3])
+def test_subtree_levels_with_many_live_cells(d):
+    """One cell of the subtree kernel's full capacity split down to single
+    points: its deep levels hold more live cells than the kernel's
+    shared-memory cell table, so their cells are kept in global memory."""
+    from paper_2201_08288_gb300 import kdt
+    cap = kdt.kdt_subtree_capacity(d)
+    assert cap >= 1024
+    rng = np.random.default_rng(40 + d)
+    pts = rng.standard_normal((d, cap)).astype(np.float32)
+    check_against_oracle(pts, r=3, subset_mode=0, depth=0, leaf_size=1, max_levels=26, key_rule=1)
+    check_against_oracle(pts, r=3, subset_mode=0, depth=12, key_rule=0)
+
+
 def test_all_equal_points_depth_and_leaf():
     pts = np.ones((3, 20000), np.float32)
     check_against_oracle(pts, r=4, depth=5)
