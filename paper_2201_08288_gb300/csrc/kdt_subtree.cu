@@ -92,26 +92,25 @@ __device__ __forceinline__ double key_range(uint32_t lo, uint32_t hi) {
 // Widest coordinate of one cell from its per-coordinate min and max keys
 // (coordinate l in lane l % 32, slot l / 32): the largest range
 // (double)max - (double)min, 0 for equal keys, lowest coordinate on ties.
+// A range is never negative, so the bit patterns of two ranges order like the
+// ranges as unsigned integers: the argmax is taken on the high word, then the
+// low word, then the lowest coordinate, with integer warp reductions (the only
+// double arithmetic is the one subtraction per range).
 __device__ __forceinline__ int warp_pick_widest(const uint32_t (&lo)[2], const uint32_t (&hi)[2], int d) {
   const int lane = threadIdx.x & 31;
-  const double r0 = lane < d ? key_range(lo[0], hi[0]) : -1.0;
-  const double r1 = lane + 32 < d ? key_range(lo[1], hi[1]) : -1.0;
-  double rb = r0;
-  int ib = lane;
-  if (r1 > r0) {
-    rb = r1;
-    ib = lane + 32;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double orb = __shfl_xor_sync(0xffffffffu, rb, o);
-    const int oib = __shfl_xor_sync(0xffffffffu, ib, o);
-    if (orb > rb || (orb == rb && oib < ib)) {
-      rb = orb;
-      ib = oib;
+  uint64_t rb = lane < d ? (uint64_t)__double_as_longlong(key_range(lo[0], hi[0])) : 0ull;
+  uint32_t ib = lane < d ? (uint32_t)lane : 0xffffffffu;
+  if (lane + 32 < d) {
+    const uint64_t r1 = (uint64_t)__double_as_longlong(key_range(lo[1], hi[1]));
+    if (r1 > rb) {
+      rb = r1;
+      ib = (uint32_t)lane + 32u;
     }
   }
-  return ib;
+  const uint32_t rh = (uint32_t)(rb >> 32), rl = (uint32_t)rb;
+  const uint32_t mh = __reduce_max_sync(0xffffffffu, rh);
+  const uint32_t ml = __reduce_max_sync(0xffffffffu, rh == mh ? rl : 0u);
+  return (int)__reduce_min_sync(0xffffffffu, (rh == mh && rl == ml) ? ib : 0xffffffffu);
 }
 
 // Block-wide exclusive scan of the flags f[0..N) into pre[0..N], pre[N] the
