@@ -118,6 +118,7 @@ void StepNeeds::add(const kdt_params& p, const TreePlan& tp) {
   slice_cells = std::max<uint32_t>(slice_cells, (uint32_t)tp.small_max);
   widest = widest || p.key_rule == KDT_KEY_WIDEST_SPREAD;
   max_d = std::max(max_d, (int)p.d);
+  min_d = std::min(min_d, (int)p.d);
 }
 
 StepPlan plan_step(const StepNeeds& needs) {
@@ -351,7 +352,9 @@ kdt_status Engine::tick() {
             : (uint32_t)std::min<uint64_t>(big_points_ / (uint64_t)kTile + (uint64_t)big_count_ + 1,
                                            (uint64_t)plan_.max_tiles);
     launch_big_step(trees_, s_, tiles_bound, (uint32_t)nseg_bound, plan_.bigseg_cap, has_roots, root_dims_,
-                    plan_.needs.widest, plan_.needs.max_d, big_points_, plan_.grid_sub, st_);
+                    plan_.needs.widest, plan_.needs.max_d,
+                    plan_.needs.min_d == plan_.needs.max_d ? plan_.needs.max_d : 0, big_points_, plan_.grid_sub,
+                    st_);
     ENGINE_TRY(cudaGetLastError());
     root_dims_ = false;
     uint32_t counts[4];

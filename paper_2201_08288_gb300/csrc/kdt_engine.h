@@ -45,7 +45,7 @@ struct StepNeeds {
   uint64_t points = 0, maxB = 0, cap_small = 0, nseg = 0;
   uint32_t max_trees = 0, slice_cells = 32;
   bool widest = false;
-  int max_d = 1;
+  int max_d = 1, min_d = 1 << 30;  // min_d == max_d: every tree has the same d
   void add(const kdt_params& p, const TreePlan& tp);
 };
 

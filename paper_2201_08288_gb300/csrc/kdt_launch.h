@@ -60,14 +60,16 @@ inline int subtree_capacity(int d) {
 
 cudaError_t prepare_step_kernels();
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
-                     uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d,
+                     uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d, int uniform_d,
                      uint64_t points, uint32_t sms, cudaStream_t st);
 
 // Dynamic shared memory of the staged scatter (two CTAs per SM).
 constexpr uint32_t kScatterSmemBytes = 100 * 1024;
 cudaError_t prepare_scatter_kernel();
+// uniform_d: the coordinate count of every tree of the step, 0 if they differ
+// (a kernel compiled for that d is used where there is one)
 void launch_scatter(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t grid_cap,
-                    uint64_t points, cudaStream_t st);
+                    uint64_t points, int uniform_d, cudaStream_t st);
 
 cudaError_t prepare_subtree_kernel();
 void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head, LCell* slices,

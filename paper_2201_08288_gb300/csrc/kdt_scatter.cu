@@ -72,6 +72,9 @@ __device__ __forceinline__ uint32_t meta_subset(const SubMeta& m, uint32_t orig)
   return (uint32_t)(((uint64_t)orig * (uint64_t)m.r) / (uint64_t)m.tn);
 }
 
+// kD > 0: compiled for trees of kD coordinates (the column loops unroll);
+// kD = 0: any d.
+template <int kD>
 __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, StepDev s) {
   extern __shared__ __align__(128) uint32_t sm[];
   __shared__ __align__(8) uint64_t full[2], empty[2];
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         c_next = s.cells[tl_next.x];
       }
       const TreeDev& tg = trees[c.tree];
-      const int d = tg.d, ncols = d + 1;
+      const int d = kD > 0 ? kD : tg.d, ncols = d + 1;
       const bool expl = tg.subset_mode == SUB_EXPLICIT;
       const int es = expl ? tg.sid_bytes : 0;
       const uint32_t T = sub_tile(ncols, es), stride = T + 4;
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       named_sync(kConsumerBar, kCT);
       if (s_fail) return;
       const SubMeta& m = meta[b];
-      const int d = m.d;
+      const int d = kD > 0 ? kD : m.d;
       const int64_t n = m.n;
       const uint32_t T = m.T, stride = T + 4, mcnt = m.mcnt, L = m.L;
       const uint32_t cbeg = m.cell_begin, ccount = m.cell_count;
@@ -450,16 +453,28 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
 
 }  // namespace
 
+template <int kD>
+cudaError_t prepare_one() {
+  return cudaFuncSetAttribute(k_scatter_tma<kD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmemBytes);
+}
+
 cudaError_t prepare_scatter_kernel() {
-  return cudaFuncSetAttribute(k_scatter_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kScatterSmemBytes);
+  for (cudaError_t e : {prepare_one<0>(), prepare_one<2>(), prepare_one<3>(), prepare_one<8>(), prepare_one<16>()})
+    if (e != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 void launch_scatter(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t grid_cap,
-                    uint64_t points, cudaStream_t st) {
+                    uint64_t points, int uniform_d, cudaStream_t st) {
   TraceScope ts(K_PART_SCATTER, st, points);
   const uint32_t grid = std::max<uint32_t>(1, std::min(max_tiles, grid_cap));
-  k_scatter_tma<<<grid, kST, kScatterSmemBytes, st>>>(trees, s);
+  switch (uniform_d) {
+    case 2: k_scatter_tma<2><<<grid, kST, kScatterSmemBytes, st>>>(trees, s); break;
+    case 3: k_scatter_tma<3><<<grid, kST, kScatterSmemBytes, st>>>(trees, s); break;
+    case 8: k_scatter_tma<8><<<grid, kST, kScatterSmemBytes, st>>>(trees, s); break;
+    case 16: k_scatter_tma<16><<<grid, kST, kScatterSmemBytes, st>>>(trees, s); break;
+    default: k_scatter_tma<0><<<grid, kST, kScatterSmemBytes, st>>>(trees, s); break;
+  }
 }
 
 }  // namespace kdt

@@ -774,7 +774,7 @@ cudaError_t prepare_step_kernels() {
 }
 
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
-                     uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d,
+                     uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d, int uniform_d,
                      uint64_t points, uint32_t sms, cudaStream_t st) {
   const uint32_t nc = s.ncells;
   if (nc == 0) return;
@@ -806,7 +806,7 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
   { TraceScope ts(K_PART_COUNT, st, points); k_part_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
   { TraceScope ts(K_PART_SCAN, st); k_part_scan<<<nc, 1024, 0, st>>>(s); }
   { TraceScope ts(K_CLASSIFY, st); k_classify<<<(nc + 255) / 256, 256, 0, st>>>(trees, s); }
-  launch_scatter(trees, s, max_tiles, 2 * sms, points, st);
+  launch_scatter(trees, s, max_tiles, 2 * sms, points, uniform_d, st);
   if (any_widest) { TraceScope ts(K_CHILD_DIMS, st); k_child_dims<<<(nc + 7) / 8, 256, 0, st>>>(trees, s); }
 }
 
