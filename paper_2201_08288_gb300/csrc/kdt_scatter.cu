@@ -86,6 +86,11 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
   __shared__ uint32_t s_fail;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ntiles = *s.ntiles_total;
+  // this CTA's contiguous range of tiles: consecutive tiles mostly share a
+  // cell, so the per-cell min / max stay in the CTA for long runs
+  const uint32_t t_begin = (uint32_t)(((uint64_t)blockIdx.x * ntiles) / gridDim.x);
+  const uint32_t t_end = (uint32_t)(((uint64_t)(blockIdx.x + 1) * ntiles) / gridDim.x);
+  for (int j = tid; j < 2 * kMaxDims * 2; j += kST) (&tmm[0][0][0])[j] = (j & 1) ? 0u : 0xffffffffu;
   if (tid == 0) {
     mbar_init(&full[0], 1);
     mbar_init(&full[1], 1);
@@ -101,13 +106,13 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
     uint32_t ephase = 0u;  // bit b: parity of buffer b's next "empty" phase
     uint32_t k = 0;
     // the next tile's record and cell are loaded one tile ahead
-    uint2 tl_next = blockIdx.x < ntiles ? s.tiles[blockIdx.x] : make_uint2(0, 0);
+    uint2 tl_next = t_begin < t_end ? s.tiles[t_begin] : make_uint2(0, 0);
     Cell c_next = s.cells[tl_next.x];
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (uint32_t tile = t_begin; tile < t_end; ++tile) {
       const uint2 tl = tl_next;
       const Cell c = c_next;
-      if (tile + gridDim.x < ntiles) {
-        tl_next = s.tiles[tile + gridDim.x];
+      if (tile + 1 < t_end) {
+        tl_next = s.tiles[tile + 1];
         c_next = s.cells[tl_next.x];
       }
       const TreeDev& tg = trees[c.tree];
@@ -243,9 +248,23 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
   uint32_t fphase = 0u;  // bit b: parity of buffer b's next "full" phase
   uint32_t lnext = 0, rnext = 0;
   bool saw_nan = false;
-  bool fresh = true;  // tmm holds nothing yet of the current cell
+  // For a compile-time d of at most 8 every lane keeps the min / max of its
+  // points per coordinate and child over the whole run of the cell's tiles
+  // (registers), reduced over the warp once at the run's end; otherwise the
+  // warps reduce after every sub-tile.
+  constexpr bool kAcc = kD > 0 && kD <= 8;
+  constexpr int kAD = kAcc ? kD : 1;
+  const float inf = __int_as_float(0x7f800000);
+  float acc[kAD][2][2];  // [coordinate][child][min, max]
+#pragma unroll
+  for (int l = 0; l < kAD; ++l)
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      acc[l][side][0] = inf;
+      acc[l][side][1] = -inf;
+    }
   uint32_t k = 0;
-  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (uint32_t tile = t_begin; tile < t_end; ++tile) {
     for (bool more = true; more; ++k) {
       const int b = k & 1;
       if (!mbar_wait_bounded(&full[b], (fphase >> b) & 1u)) atomicExch(&s_fail, 1u);
@@ -264,11 +283,6 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       if (m.sub == m.tile_start) {
         lnext = cbeg + m.loff;
         rnext = cbeg + L + (m.tile_start - m.loff);
-        if (want_mm && fresh)
-          for (int j = tid; j < 4 * d; j += kCT) {
-            const int side = j / (2 * d), l = (j / 2) % d, which = j & 1;
-            tmm[side][l][which] = which ? 0u : 0xffffffffu;
-          }
       }
       const uint32_t* A = sm + (size_t)b * (kBufBytes / 4);
       const uint8_t* SA = (const uint8_t*)(A + (size_t)(d + 1) * stride) + (size_t)m.sid_ph * m.sid_bytes;
@@ -326,6 +340,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       }
 
       // ---- coordinate columns, two at a time, straight from shared memory
+#pragma unroll
       for (int c = 0; c < d; c += 2) {
         const bool two = c + 1 < d;
         const uint32_t* a0 = A + (size_t)c * stride + m.ph[c];
@@ -350,10 +365,33 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
             o0[dst[q]] = __uint_as_float(v0[q]);
             if (two) o1[dst[q]] = __uint_as_float(v1[q]);
           }
-        if (want_mm) {
+        if (want_mm && kAcc) {
           // min / max as floats (the widest rule only uses max - min, which -0
-          // and +0 do not change); keys are formed once per warp below
-          const float inf = __int_as_float(0x7f800000);
+          // and +0 do not change); keys are formed at the run's end
+          const int c1 = two ? c + 1 : c;
+#pragma unroll
+          for (int q = 0; q < kMaxItems; ++q)
+            if (keep[q]) {
+              const float x0 = __uint_as_float(v0[q]), x1 = __uint_as_float(v1[q]);
+              const int side = left[q] ? 0 : 1;
+              if (side == 0) {
+                acc[c % kAD][0][0] = fminf(acc[c % kAD][0][0], x0);
+                acc[c % kAD][0][1] = fmaxf(acc[c % kAD][0][1], x0);
+                if (two) {
+                  acc[c1 % kAD][0][0] = fminf(acc[c1 % kAD][0][0], x1);
+                  acc[c1 % kAD][0][1] = fmaxf(acc[c1 % kAD][0][1], x1);
+                }
+              } else {
+                acc[c % kAD][1][0] = fminf(acc[c % kAD][1][0], x0);
+                acc[c % kAD][1][1] = fmaxf(acc[c % kAD][1][1], x0);
+                if (two) {
+                  acc[c1 % kAD][1][0] = fminf(acc[c1 % kAD][1][0], x1);
+                  acc[c1 % kAD][1][1] = fmaxf(acc[c1 % kAD][1][1], x1);
+                }
+              }
+            }
+        } else if (want_mm) {
+          // min / max as floats, then keys once per warp and sub-tile
           float mm[2][2][2] = {{{inf, -inf}, {inf, -inf}}, {{inf, -inf}, {inf, -inf}}};  // [col][side][min,max]
 #pragma unroll
           for (int q = 0; q < kMaxItems; ++q)
@@ -430,15 +468,31 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         if (want_mm) {
           // keep reducing while this CTA's next tile is of the same cell;
           // else add the run's min / max to the cell's with atomics
-          const uint32_t nt = tile + gridDim.x;
-          const bool same = nt < ntiles && s.tiles[nt].x == m.cell_idx;
-          fresh = !same;
+          const uint32_t nt = tile + 1;
+          const bool same = nt < t_end && s.tiles[nt].x == m.cell_idx;
           if (!same) {
+            if (kAcc) {
+#pragma unroll
+              for (int l = 0; l < kAD; ++l)
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                  const uint32_t lo = __reduce_min_sync(0xffffffffu, ord_key(acc[l][side][0]));
+                  const uint32_t hi = __reduce_max_sync(0xffffffffu, ord_key(acc[l][side][1]));
+                  if (lane == 0) {
+                    atomic_min_shared(&tmm[side][l][0], lo);
+                    atomic_max_shared(&tmm[side][l][1], hi);
+                  }
+                  acc[l][side][0] = inf;
+                  acc[l][side][1] = -inf;
+                }
+            }
             named_sync(kConsumerBar, kCT);
+            // add the run's min / max to the cell's; reset the table
             for (int j = tid; j < 4 * d; j += kCT) {
               const int side = j / (2 * d), l = (j / 2) % d, which = j & 1;
               uint32_t* dst = &s.child_mm[(((size_t)m.cell_idx * 2 + side) * kMaxDims + l) * 2 + which];
               if (which) atomicMax(dst, tmm[side][l][which]); else atomicMin(dst, tmm[side][l][which]);
+              tmm[side][l][which] = which ? 0u : 0xffffffffu;
             }
           }
         }
