@@ -622,6 +622,29 @@ __global__ void __launch_bounds__(256) k_combine(const TreeDev* trees, StepDev s
   }
 }
 
+// One warp per cell (steps with many cells): the same weighted lower median
+// by the warp radix select, which starts at the first bit where the cell's
+// segment medians differ.
+__global__ void __launch_bounds__(256) k_combine_warp(const TreeDev* trees, StepDev s) {
+  __shared__ uint32_t hist[8][256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t c = blockIdx.x * 8u + (uint32_t)warp;
+  if (c >= s.ncells) return;
+  const Cell cell = s.cells[c];
+  const TreeDev& t = trees[cell.tree];
+  const uint32_t g0 = s.seg_base[c];
+  const uint32_t* med = s.seg_med + g0;
+  const uint32_t* wt = s.seg_w + g0;
+  const uint32_t m = warp_weighted_select(
+      (uint32_t)t.r, (cell.count - 1) / 2, hist[warp], [&](uint32_t j) { return med[j]; },
+      [&](uint32_t j) { return wt[j]; }, [&](uint32_t j) { return wt[j] != 0u; });
+  if (lane == 0) {
+    s.mkey[c] = m;
+    t.out_vals[cell.heap] = key_float(m);
+    t.out_dims[cell.heap] = (int8_t)s.kdim[c];
+  }
+}
+
 // ------------------------------------------------------------ partition
 
 // Per tile: number of points with key <= split.
@@ -671,6 +694,23 @@ __global__ void k_part_scan(StepDev s) {
     run += tot;
   }
   if (threadIdx.x == 0) s.lcount[c] = run;
+}
+
+// One warp per cell (steps with many cells, few tiles each).
+__global__ void __launch_bounds__(256) k_part_scan_warp(StepDev s) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t c = blockIdx.x * 8u + (uint32_t)warp;
+  if (c >= s.ncells) return;
+  const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
+  uint32_t run = 0;
+  for (uint32_t j0 = tb; j0 < te; j0 += 32) {
+    const uint32_t j = j0 + (uint32_t)lane;
+    const uint32_t v = j < te ? s.tile_left[j] : 0u;
+    const uint32_t inc = warp_incl_scan(v);
+    if (j < te) s.tile_loff[j] = run + inc - v;
+    run += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (lane == 0) s.lcount[c] = run;
 }
 
 // One warp per cell (widest spread): the key coordinate of each big child
@@ -769,6 +809,8 @@ __global__ void k_classify(const TreeDev* trees, StepDev s) {
 
 // ------------------------------------------------------------ launcher
 
+constexpr uint32_t kManyCells = 1024;  // from here on: a warp per cell in combine and scan
+
 cudaError_t prepare_step_kernels() {
   return cudaFuncSetAttribute(k_ps_move, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPsSmemBytes);
 }
@@ -802,9 +844,24 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
     TraceScope ts(K_SELECT_BIG, st);
     k_select_big<<<std::max<uint32_t>(1, std::min<uint32_t>(max_bigseg, sms * 4u)), 256, 0, st>>>(trees, s);
   }
-  { TraceScope ts(K_COMBINE, st); k_combine<<<nc, 256, 0, st>>>(trees, s); }
+  // a CTA per cell while cells are few (large subset counts, deep scans),
+  // a warp per cell once they are many
+  const bool many = nc >= kManyCells;
+  {
+    TraceScope ts(K_COMBINE, st);
+    if (many)
+      k_combine_warp<<<(nc + 7) / 8, 256, 0, st>>>(trees, s);
+    else
+      k_combine<<<nc, 256, 0, st>>>(trees, s);
+  }
   { TraceScope ts(K_PART_COUNT, st, points); k_part_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
-  { TraceScope ts(K_PART_SCAN, st); k_part_scan<<<nc, 1024, 0, st>>>(s); }
+  {
+    TraceScope ts(K_PART_SCAN, st);
+    if (many)
+      k_part_scan_warp<<<(nc + 7) / 8, 256, 0, st>>>(s);
+    else
+      k_part_scan<<<nc, 1024, 0, st>>>(s);
+  }
   { TraceScope ts(K_CLASSIFY, st); k_classify<<<(nc + 255) / 256, 256, 0, st>>>(trees, s); }
   launch_scatter(trees, s, max_tiles, 2 * sms, points, uniform_d, st);
   if (any_widest) { TraceScope ts(K_CHILD_DIMS, st); k_child_dims<<<(nc + 7) / 8, 256, 0, st>>>(trees, s); }

@@ -96,6 +96,17 @@ def test_dims_around_subtree_capacity(d):
         check_against_oracle(pts, r=5, subset_mode=0, depth=6, key_rule=d % 2)
 
 
+def test_big_steps_with_many_cells():
+    """d = 16 (subtree capacity 1056) and cells of about 1100 points at level
+    10: more than a thousand big cells in one step, where the combine and the
+    tile scan run a warp per cell."""
+    from paper_2201_08288_gb300 import kdt
+    assert kdt.kdt_subtree_capacity(16) < 1100
+    n, d = 1024 * 1100, 16
+    pts = np.random.default_rng(11).standard_normal((d, n)).astype(np.float32)
+    check_against_oracle(pts, r=8, subset_mode=0, depth=11, key_rule=1)
+
+
 @pytest.mark.parametrize("d", [1, 3])
 def test_subtree_levels_with_many_live_cells(d):
     """One cell of the subtree kernel's full capacity split down to single
