@@ -534,36 +534,66 @@ __global__ void __launch_bounds__(256) k_select_small(const TreeDev* trees, Step
 }
 
 // CTAs stride over the listed segments above kSelSmallMax points: 8-bit MSD
-// radix select with a CTA-wide histogram, keys read from global memory.
+// radix select, keys read from global memory 16 bytes at a time (the
+// unaligned head and tail of the segment by single words), counted into one
+// histogram per warp (the top digits of clustered data fall into few bins),
+// which are summed bin by bin before the digit is chosen.
 __global__ void __launch_bounds__(256) k_select_big(const TreeDev* trees, StepDev s) {
-  __shared__ uint32_t hist[256];
+  constexpr int kW = 8;
+  __shared__ uint32_t hist[kW][256];
+  __shared__ uint32_t tot[256];
   __shared__ uint32_t bcast[2];
+  const int warp = threadIdx.x >> 5;
   const uint32_t cnt = min(*s.bigseg_count, s.bigseg_cap);
   for (uint32_t jb = blockIdx.x; jb < cnt; jb += gridDim.x) {
     const uint32_t g = s.bigseg[jb];
     const uint32_t w = s.seg_w[g];
     const uint32_t* keys = s.seg_key[g];
+    const uint32_t head = min(w, (4u - (uint32_t)(((uintptr_t)keys >> 2) & 3u)) & 3u);
+    const uint4* kv = (const uint4*)(keys + head);  // 16-byte aligned
+    const uint32_t nv = (w - head) >> 2, tail0 = head + nv * 4u;
     uint32_t rank = (w - 1) / 2, prefix = 0, mask = 0;
     for (int shift = 24; shift >= 0; shift -= 8) {
-      for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+      for (int i = threadIdx.x; i < kW * 256; i += blockDim.x) (&hist[0][0])[i] = 0;
       __syncthreads();
-      uint32_t i = threadIdx.x;
-      for (; i + 7 * 256 < w; i += 8 * 256) {
-        uint32_t k[8];
+      uint32_t* wh = hist[warp];
+      auto add = [&](uint32_t u) {
+        const uint32_t k = ord_key(__uint_as_float(u));
+        if ((k & mask) == prefix) atomicAdd(&wh[(k >> shift) & 255u], 1u);
+      };
+      uint32_t v = threadIdx.x;
+      for (; v + 3 * 256 < nv; v += 4 * 256) {
+        uint4 q[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) k[q] = kload(keys + i + q * 256);
+        for (int u = 0; u < 4; ++u) q[u] = __ldg(kv + v + u * 256);
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if ((k[q] & mask) == prefix) atomicAdd(&hist[(k[q] >> shift) & 255u], 1u);
+        for (int u = 0; u < 4; ++u) {
+          add(q[u].x);
+          add(q[u].y);
+          add(q[u].z);
+          add(q[u].w);
+        }
       }
-      for (; i < w; i += 256) {
-        const uint32_t k = kload(keys + i);
-        if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+      for (; v < nv; v += 256) {
+        const uint4 q = __ldg(kv + v);
+        add(q.x);
+        add(q.y);
+        add(q.z);
+        add(q.w);
+      }
+      if (threadIdx.x < head) add(__ldg(keys + threadIdx.x));
+      if (threadIdx.x < w - tail0) add(__ldg(keys + tail0 + threadIdx.x));
+      __syncthreads();
+      {
+        uint32_t sum = 0;
+#pragma unroll
+        for (int q = 0; q < kW; ++q) sum += hist[q][threadIdx.x];
+        tot[threadIdx.x] = sum;
       }
       __syncthreads();
       if (threadIdx.x < 32) {
         uint32_t below;
-        const uint32_t digit = warp_find_digit(hist, rank, &below);
+        const uint32_t digit = warp_find_digit(tot, rank, &below);
         if (threadIdx.x == 0) {
           bcast[0] = digit;
           bcast[1] = below;
@@ -573,9 +603,9 @@ __global__ void __launch_bounds__(256) k_select_big(const TreeDev* trees, StepDe
       rank -= bcast[1];
       prefix |= bcast[0] << shift;
       mask |= 255u << shift;
-      __syncthreads();
     }
     if (threadIdx.x == 0) s.seg_med[g] = prefix;
+    __syncthreads();
   }
 }
 
