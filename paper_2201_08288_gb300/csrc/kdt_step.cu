@@ -498,10 +498,85 @@ __device__ uint32_t warp_bitonic_median(const uint32_t* keys, uint32_t w) {
   return __shfl_sync(0xffffffffu, x, want % 32u);
 }
 
+// State of a warp's radix select: the key bits found so far (`prefix`, all
+// bits above `rem`) and the rank still sought below them.
+struct RadixState {
+  uint32_t prefix, rank;
+  int rem;
+};
+
+__device__ __forceinline__ bool radix_start(uint32_t lo, uint32_t hi, uint32_t rank, RadixState* st) {
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  st->rank = rank;
+  if (lo >= hi) {
+    st->prefix = lo;
+    st->rem = 0;
+    return false;
+  }
+  st->rem = 32 - __clz(lo ^ hi);
+  st->prefix = st->rem == 32 ? 0u : (lo & ~((1u << st->rem) - 1u));
+  return true;
+}
+
+// Lower median (rank (w-1)/2) of w keys by one warp: MSD radix select with
+// 8-bit digits over the bits where the keys differ (histogram of 256 words
+// owned by the warp), the keys read on every pass from global memory (raw
+// float bits, turned into order keys), 8 loads per lane issued together, or
+// from a shared-memory copy (order keys already).
+template <bool kGlobal>
+__device__ uint32_t warp_select_stream(const uint32_t* keys, uint32_t w, uint32_t* hist) {
+  constexpr int U = 8;
+  const int lane = threadIdx.x & 31;
+  auto load = [&](uint32_t i) -> uint32_t { return kGlobal ? kload(keys + i) : keys[i]; };
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  for (uint32_t b0 = 0; b0 < w; b0 += 32 * U) {
+    uint32_t x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t i = b0 + (uint32_t)(u * 32 + lane);
+      x[u] = i < w ? load(i) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (b0 + (uint32_t)(u * 32 + lane) < w) {
+        lo = min(lo, x[u]);
+        hi = max(hi, x[u]);
+      }
+  }
+  RadixState st;
+  if (!radix_start(lo, hi, (w - 1) / 2, &st)) return st.prefix;
+  while (st.rem > 0) {
+    const int bits = st.rem < 8 ? st.rem : 8, shift = st.rem - bits;
+    const uint32_t nb = 1u << bits, hmask = st.rem == 32 ? 0u : ~((1u << st.rem) - 1u);
+    for (uint32_t i = lane; i < nb; i += 32) hist[i] = 0;
+    __syncwarp();
+    for (uint32_t b0 = 0; b0 < w; b0 += 32 * U) {
+      uint32_t x[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t i = b0 + (uint32_t)(u * 32 + lane);
+        x[u] = i < w ? load(i) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (b0 + (uint32_t)(u * 32 + lane) < w && (x[u] & hmask) == st.prefix)
+          atomicAdd(&hist[(x[u] >> shift) & (nb - 1u)], 1u);
+    }
+    __syncwarp();
+    uint32_t below;
+    const uint32_t digit = warp_find_digit_n(hist, nb, st.rank, &below);
+    st.rank -= below;
+    st.prefix |= digit << shift;
+    st.rem = shift;
+    __syncwarp();
+  }
+  return st.prefix;
+}
+
 // One warp per listed segment of kSelTinyMax+1 .. kSelSmallMax points: up to
-// 256 keys sorted in registers; larger segments: keys staged once in shared
-// memory (up to 1024 of them), then a radix select over the bits where they
-// differ.
+// 256 keys sorted in registers; up to 1024 keys staged once in shared memory
+// for a radix select; larger segments read from global memory on every pass.
 __global__ void __launch_bounds__(256) k_select_small(const TreeDev* trees, StepDev s) {
   __shared__ uint32_t hist[8][256];
   __shared__ uint32_t stage[8][1024];
@@ -520,13 +595,23 @@ __global__ void __launch_bounds__(256) k_select_small(const TreeDev* trees, Step
       med = warp_bitonic_median<8>(keys, w);
     } else if (w <= 1024u) {
       uint32_t* st = stage[warp];
-      for (uint32_t i = lane; i < w; i += 32) st[i] = kload(keys + i);
+      for (uint32_t b0 = 0; b0 < w; b0 += 256) {
+        uint32_t x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint32_t i = b0 + (uint32_t)(u * 32 + lane);
+          x[u] = i < w ? kload(keys + i) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint32_t i = b0 + (uint32_t)(u * 32 + lane);
+          if (i < w) st[i] = x[u];
+        }
+      }
       __syncwarp();
-      med = warp_weighted_select<true>(w, (w - 1) / 2, hist[warp], [&](uint32_t i) { return st[i]; },
-                                       [](uint32_t) { return 1u; });
+      med = warp_select_stream<false>(st, w, hist[warp]);
     } else {
-      med = warp_weighted_select<true>(w, (w - 1) / 2, hist[warp], [&](uint32_t i) { return kload(keys + i); },
-                                       [](uint32_t) { return 1u; });
+      med = warp_select_stream<true>(keys, w, hist[warp]);
     }
     if (lane == 0) s.seg_med[g] = med;
     __syncwarp();
