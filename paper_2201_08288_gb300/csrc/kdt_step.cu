@@ -323,27 +323,53 @@ __device__ __forceinline__ double key_range(uint32_t lo, uint32_t hi) {
 }
 
 // One CTA per cell with an unknown widest coordinate: reduce the tile
-// partials and pick the coordinate of largest range (lowest on ties).
-__global__ void k_pick_dim(const TreeDev* trees, StepDev s) {
+// partials and pick the coordinate of largest range (lowest on ties). Every
+// thread walks its own tiles, eight coordinates at a time (four 16-byte loads
+// per tile: a tile's record holds min, max of each coordinate in turn).
+__global__ void __launch_bounds__(1024) k_pick_dim(const TreeDev* trees, StepDev s) {
   const uint32_t c = blockIdx.x;
   const Cell cell = s.cells[c];
   const TreeDev& t = trees[cell.tree];
   if (t.key_rule != KEY_WIDEST || cell.dim >= 0) return;
   __shared__ uint32_t slo[kMaxDims], shi[kMaxDims];
+  for (int l = threadIdx.x; l < t.d; l += blockDim.x) {
+    slo[l] = 0xffffffffu;
+    shi[l] = 0u;
+  }
+  __syncthreads();
   const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int l = warp; l < t.d; l += nw) {
-    uint32_t lo = 0xffffffffu, hi = 0u;
-    for (uint32_t j = tb + lane; j < te; j += 32) {
-      lo = min(lo, s.tile_mm[((size_t)j * 2 * kMaxDims + l) * 2 + 0]);
-      hi = max(hi, s.tile_mm[((size_t)j * 2 * kMaxDims + l) * 2 + 1]);
+  const int lane = threadIdx.x & 31;
+  for (int c0 = 0; c0 < t.d; c0 += 8) {
+    const int nc = min(8, t.d - c0);
+    uint32_t lo[8], hi[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      lo[q] = 0xffffffffu;
+      hi[q] = 0u;
     }
-    lo = warp_min(lo);
-    hi = warp_max(hi);
-    if (lane == 0) {
-      slo[l] = lo;
-      shi[l] = hi;
+    for (uint32_t j = tb + threadIdx.x; j < te; j += blockDim.x) {
+      // 16-byte aligned: a record is 2 * kMaxDims * 2 words, c0 a multiple of 8
+      const uint4* p = (const uint4*)(s.tile_mm + ((size_t)j * 2 * kMaxDims + c0) * 2);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        if (2 * h >= nc) break;
+        const uint4 v = p[h];
+        lo[2 * h] = min(lo[2 * h], v.x);
+        hi[2 * h] = max(hi[2 * h], v.y);
+        lo[2 * h + 1] = min(lo[2 * h + 1], v.z);
+        hi[2 * h + 1] = max(hi[2 * h + 1], v.w);
+      }
     }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < nc) {
+        const uint32_t l2 = __reduce_min_sync(0xffffffffu, lo[q]);
+        const uint32_t h2 = __reduce_max_sync(0xffffffffu, hi[q]);
+        if (lane == 0) {
+          atomic_min_shared(&slo[c0 + q], l2);
+          atomic_max_shared(&shi[c0 + q], h2);
+        }
+      }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -762,28 +788,34 @@ __global__ void __launch_bounds__(256) k_combine_warp(const TreeDev* trees, Step
 
 // ------------------------------------------------------------ partition
 
-// Per tile: number of points with key <= split.
+// Per tile: number of points with key <= split. The tile's key range is
+// read 16 bytes at a time (its unaligned head and tail by single words).
 __global__ void __launch_bounds__(kTileThreads) k_part_count(const TreeDev* trees, StepDev s) {
   uint2 tl;
   if (!tile_of(s, blockIdx.x, &tl)) return;
   __shared__ uint32_t red[kWarps];
   const Cell cell = s.cells[tl.x];
   const TreeDev& t = trees[cell.tree];
-  const float* X = src_cols(t, cell.level) + (int64_t)s.kdim[tl.x] * t.n + cell.begin;
+  const float* X = src_cols(t, cell.level) + (int64_t)s.kdim[tl.x] * t.n + cell.begin + tl.y;
   const uint32_t m = s.mkey[tl.x];
-  const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
-  float x[kItems];
+  const uint32_t cnt_pts = min((uint32_t)kTile, cell.count - tl.y);
+  const uint32_t head = min(cnt_pts, (4u - (uint32_t)(((uintptr_t)X >> 2) & 3u)) & 3u);
+  const uint32_t nv = (cnt_pts - head) >> 2, tail0 = head + nv * 4u;
+  const float4* xv = (const float4*)(X + head);  // 16-byte aligned
+  constexpr int kV = kItems / 4;                 // vectors per thread of a full tile
+  float4 v[kV];
 #pragma unroll
-  for (int q = 0; q < kItems; ++q) {
-    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-    x[q] = i < end ? X[i] : 0.0f;
+  for (int q = 0; q < kV; ++q) {
+    const uint32_t i = threadIdx.x + q * kTileThreads;
+    v[q] = i < nv ? __ldg(xv + i) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   uint32_t cnt = 0;
 #pragma unroll
-  for (int q = 0; q < kItems; ++q) {
-    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-    cnt += (i < end) && ord_key(x[q]) <= m;
-  }
+  for (int q = 0; q < kV; ++q)
+    if (threadIdx.x + q * kTileThreads < nv)
+      cnt += (ord_key(v[q].x) <= m) + (ord_key(v[q].y) <= m) + (ord_key(v[q].z) <= m) + (ord_key(v[q].w) <= m);
+  if (threadIdx.x < head) cnt += ord_key(__ldg(X + threadIdx.x)) <= m;
+  if (threadIdx.x < cnt_pts - tail0) cnt += ord_key(__ldg(X + tail0 + threadIdx.x)) <= m;
   cnt = __reduce_add_sync(0xffffffffu, cnt);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
   __syncthreads();
@@ -944,7 +976,7 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
   }
   if (need_root_dims) {
     { TraceScope ts(K_MINMAX, st, points); k_minmax<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
-    { TraceScope ts(K_PICK_DIM, st); k_pick_dim<<<nc, 256, 0, st>>>(trees, s); }
+    { TraceScope ts(K_PICK_DIM, st); k_pick_dim<<<nc, 1024, 0, st>>>(trees, s); }
   }
   { TraceScope ts(K_SEGS, st); k_segs<<<nc, 256, 0, st>>>(trees, s); }
   {
