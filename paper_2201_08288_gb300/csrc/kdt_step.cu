@@ -182,17 +182,27 @@ __global__ void __launch_bounds__(kPsThreads) k_ps_move(const TreeDev* trees, St
   uint2 tl;
   Cell cell;
   if (!presort_tile(trees, s, blockIdx.x, &tl, &cell)) return;
-  if ((tl.y / (uint32_t)kTile) % (uint32_t)kPsGroup != 0u) return;  // the group's first tile runs it
   const TreeDev& t = trees[cell.tree];
+  // widest spread: the group's min / max key per coordinate go to the record
+  // of its first tile, the other tiles' records hold the identities
+  const bool want_mm = t.key_rule == KEY_WIDEST && cell.dim < 0;
+  if ((tl.y / (uint32_t)kTile) % (uint32_t)kPsGroup != 0u) {  // the group's first tile runs it
+    if (want_mm)
+      for (int j = threadIdx.x; j < 2 * t.d; j += blockDim.x)
+        s.tile_mm[((size_t)blockIdx.x * 2 * kMaxDims + j / 2) * 2 + (j & 1)] = (j & 1) ? 0u : 0xffffffffu;
+    return;
+  }
   extern __shared__ __align__(16) uint32_t ps_buf[];  // kPsPoints words, then kPsPoints u16 subsets
   uint16_t* lsub = (uint16_t*)(ps_buf + kPsPoints);
   __shared__ uint32_t loff[kMaxSubsets];   // counts, then local offsets
   __shared__ uint32_t gbase[kMaxSubsets];  // global start of each subset's run
   __shared__ uint32_t tmp[33];
+  __shared__ uint32_t gmm[kMaxDims][2];
   const uint32_t r = (uint32_t)t.r, i0 = tl.y, end = min(i0 + (uint32_t)kPsPoints, cell.count);
   const uint32_t m = end - i0;
   const bool expl = t.subset_mode == SUB_EXPLICIT;
   for (uint32_t j = threadIdx.x; j < r; j += kPsThreads) loff[j] = 0;
+  for (int j = threadIdx.x; j < 2 * t.d; j += kPsThreads) gmm[j / 2][j & 1] = (j & 1) ? 0u : 0xffffffffu;
   __syncthreads();
   uint32_t sub[kPsItems], lp[kPsItems];
 #pragma unroll
@@ -240,17 +250,43 @@ __global__ void __launch_bounds__(kPsThreads) k_ps_move(const TreeDev* trees, St
     __syncthreads();
   };
   const int64_t n = t.n;
-  for (int l = 0; l < t.d; ++l) {
+  // each column's loads are issued before the previous column's passes
+  uint32_t x[kPsItems], xn[kPsItems];
+  auto load = [&](int l, uint32_t (&v)[kPsItems]) {
     const uint32_t* X = (const uint32_t*)(t.x_in + (int64_t)l * n);
-    uint32_t x[kPsItems];
 #pragma unroll
     for (int q = 0; q < kPsItems; ++q) {
       const uint32_t i = i0 + threadIdx.x + q * kPsThreads;
-      x[q] = i < end ? X[i] : 0u;
+      v[q] = i < end ? __ldg(X + i) : 0u;
+    }
+  };
+  load(0, x);
+  for (int l = 0; l < t.d; ++l) {
+    if (l + 1 < t.d) load(l + 1, xn);
+    if (want_mm) {
+      uint32_t lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+      for (int q = 0; q < kPsItems; ++q)
+        if (sub[q] != 0xffffffffu) {
+          const uint32_t k = ord_key(__uint_as_float(x[q]));
+          lo = min(lo, k);
+          hi = max(hi, k);
+        }
+      lo = __reduce_min_sync(0xffffffffu, lo);
+      hi = __reduce_max_sync(0xffffffffu, hi);
+      if ((threadIdx.x & 31) == 0) {
+        atomic_min_shared(&gmm[l][0], lo);
+        atomic_max_shared(&gmm[l][1], hi);
+      }
     }
     uint32_t* out = (uint32_t*)(t.xbuf[1] + (int64_t)l * n);
     pass([&](int q) { return x[q]; }, [&](uint32_t dst, uint32_t v) { out[dst] = v; });
+#pragma unroll
+    for (int q = 0; q < kPsItems; ++q) x[q] = xn[q];
   }
+  if (want_mm)  // the passes' barriers order the shared-memory reductions before this
+    for (int j = threadIdx.x; j < 2 * t.d; j += kPsThreads)
+      s.tile_mm[((size_t)blockIdx.x * 2 * kMaxDims + j / 2) * 2 + (j & 1)] = gmm[j / 2][j & 1];
   pass([&](int q) { return i0 + threadIdx.x + q * kPsThreads; },
        [&](uint32_t dst, uint32_t v) { t.pbuf[1][dst] = v; });
   if (expl) {
@@ -271,7 +307,7 @@ __global__ void __launch_bounds__(kTileThreads) k_minmax(const TreeDev* trees, S
   if (!tile_of(s, blockIdx.x, &tl)) return;
   const Cell cell = s.cells[tl.x];
   const TreeDev& t = trees[cell.tree];
-  if (t.key_rule != KEY_WIDEST || cell.dim >= 0) return;
+  if (t.key_rule != KEY_WIDEST || cell.dim >= 0 || t.presorted) return;  // presorted: from k_ps_move
   __shared__ uint32_t red[2][kWarps];
   const float* X = src_cols(t, cell.level) + cell.begin;
   const int64_t n = t.n;
