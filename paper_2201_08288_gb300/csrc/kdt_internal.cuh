@@ -157,7 +157,8 @@ struct StepDev {
   uint32_t bigseg_cap;
   uint32_t midseg_cap;
   uint32_t pad4;
-  uint2* crow;                // [ncells][2] (slot, row of off_next) of each big child, else kNoRow
+  uint2* crow;                // [ncells][2] (slot, row of off_next) of each big child; (kNoRow, slot in
+                              // small) of a child queued for the subtree kernel; else (kNoRow, kNoRow)
 };
 
 constexpr uint32_t kNoRow = 0xffffffffu;

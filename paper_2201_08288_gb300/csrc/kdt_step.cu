@@ -896,8 +896,9 @@ __global__ void __launch_bounds__(256) k_part_scan_warp(StepDev s) {
   if (lane == 0) s.lcount[c] = run;
 }
 
-// One warp per cell (widest spread): the key coordinate of each big child
-// from its min and max key per coordinate (reduced by the scatter): the
+// One warp per cell (widest spread): the key coordinate of each big child,
+// and of each child queued for the subtree kernel (its first level), from its
+// min and max key per coordinate (reduced by the scatter): the
 // largest range (double)max - (double)min, 0 for equal keys, lowest
 // coordinate on ties.
 __global__ void __launch_bounds__(256) k_child_dims(const TreeDev* trees, StepDev s) {
@@ -910,7 +911,7 @@ __global__ void __launch_bounds__(256) k_child_dims(const TreeDev* trees, StepDe
   const int d = t.d;
   for (int side = 0; side < 2; ++side) {
     const uint2 cr = s.crow[2 * c + side];
-    if (cr.x == kNoRow) continue;
+    if (cr.x == kNoRow && cr.y == kNoRow) continue;  // terminal
     double rb = -1.0;
     int ib = 0;
     for (int l = lane; l < d; l += 32) {
@@ -930,7 +931,12 @@ __global__ void __launch_bounds__(256) k_child_dims(const TreeDev* trees, StepDe
         ib = oib;
       }
     }
-    if (lane == 0) s.next_big[cr.x].dim = (int16_t)ib;
+    if (lane == 0) {
+      if (cr.x != kNoRow)
+        s.next_big[cr.x].dim = (int16_t)ib;
+      else
+        s.small[cr.y].dim = (int16_t)ib;  // the subtree kernel's first level
+    }
   }
 }
 
@@ -968,7 +974,12 @@ __global__ void k_classify(const TreeDev* trees, StepDev s) {
       const Cell child{cb[side], cc[side], heap, cell.tree, (int8_t)level, (int8_t)stall, (int16_t)-1};
       if (cc[side] <= (uint32_t)t.small_max) {
         const uint32_t slot = atomicAdd(s.small_count, 1u);
-        if (slot < s.small_cap) s.small[slot] = child; else set_status(t, ST_CAPACITY);
+        if (slot < s.small_cap) {
+          s.small[slot] = child;
+          cr = make_uint2(kNoRow, slot);  // its widest coordinate is picked with the big children's
+        } else {
+          set_status(t, ST_CAPACITY);
+        }
         atomicAdd(s.small_points, cc[side]);
       } else {
         const uint32_t slot = atomicAdd(s.next_big_count, 1u);

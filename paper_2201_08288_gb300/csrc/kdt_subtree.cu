@@ -215,6 +215,14 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
       uint32_t* pm0 = S.cols + s_colbase[d];
       if (!P)
         for (uint32_t i = tid; i < N; i += T) pm0[i] = b0 + i;
+      // explicit subset ids are read from global memory while the bulk copies
+      // run (neither touches the other's shared memory)
+      const void* SID = src_sid(t, c.level);
+      const bool expl = t.subset_mode == SUB_EXPLICIT;
+      for (uint32_t i = tid; i < N; i += T) {
+        if (expl) S.sid[i] = (uint16_t)subset_of(t, SID, 0u, (int64_t)b0 + i);
+        S.cellid[i] = 0;
+      }
       if (!mbar_wait_bounded(&s_bar, phase)) {
         set_status(t, ST_TIMEOUT);
         atomicExch(&s_fail, 1u);
@@ -235,11 +243,8 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
         }
       }
       if (nan) set_status(t, ST_NAN_INPUT);
-      const void* SID = src_sid(t, c.level);
-      for (uint32_t i = tid; i < N; i += T) {
-        S.sid[i] = (uint16_t)subset_of(t, SID, pm0[i], (int64_t)b0 + i);
-        S.cellid[i] = 0;
-      }
+      if (!expl)
+        for (uint32_t i = tid; i < N; i += T) S.sid[i] = (uint16_t)subset_of(t, SID, pm0[i], (int64_t)b0 + i);
       // The root of a small tree arrives in index order: put it in subset
       // order (counting sort; order inside a subset is immaterial). Every
       // other cell is in subset order already.
@@ -289,6 +294,8 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head
         // ---- 1. key coordinate of every live cell
         if (t.key_rule == KEY_CYCLIC) {
           for (uint32_t k = tid; k < ncur; k += T) cc[k].dim = (uint8_t)(level % d);
+        } else if (level == (int)c.level && c.dim >= 0) {
+          if (tid == 0) cc[0].dim = (uint8_t)c.dim;  // picked from the parent's partition
         } else {
           // per (cell, part): min and max key of every coordinate, coordinate l
           // ending in lane l % 32; G warps share a cell when there are few cells
