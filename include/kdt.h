@@ -206,6 +206,48 @@ kdt_status kdt_server_stats(kdt_server *s, kdt_server_info *out);
 /* Finish the requests in flight, drop the queued ones, free the arena. */
 kdt_status kdt_server_destroy(kdt_server *s);
 
+/* ---- tuning -------------------------------------------------------------
+ * The lower median of every (cell, subset) segment (paper, Sec. 2: the
+ * medians computed independently on the r subsets) takes one of four paths by
+ * the segment's size: one thread sorting it in registers; one warp with a
+ * bitonic network; one warp with a radix select; one CTA with a radix select.
+ * Where the paths change, the CTA's size and the width of its radix digits
+ * are tunable. Every choice gives the same outputs, bit for bit: the choices
+ * trade only speed, and kdt_autotune times them on the caller's own trees.
+ */
+typedef struct kdt_tuning {
+  int32_t tiny_max;     /* one thread per segment up to this many keys: 8, 16 or 32    */
+  int32_t bitonic_max;  /* a warp's bitonic network up to this many: 64, 128 or 256    */
+  int32_t warp_max;     /* a warp's radix select up to this many: 1024, 2048 or 4096   */
+  int32_t cta_threads;  /* threads of the CTA radix select: 256 or 512                 */
+  int32_t digit_bits;   /* digit width of the CTA radix select: 8 (4 passes) or 11 (3) */
+  int32_t reserved[3];  /* zero                                                        */
+} kdt_tuning;
+
+/* The library's defaults. t: host, filled. */
+void kdt_tuning_default(kdt_tuning *t);
+/* Install t (host; NULL: the defaults) for the level steps that start after
+ * the call, in every build of this process (plain, batched, served). Errors:
+ * KDT_ERR_INVALID_ARG (a field outside its choices, reserved not zero), and
+ * the tuning in force is kept. */
+kdt_status kdt_set_tuning(const kdt_tuning *t);
+/* The tuning in force. t: host, filled. Errors: KDT_ERR_INVALID_ARG (NULL). */
+kdt_status kdt_get_tuning(kdt_tuning *t);
+/*
+ * Autotuner: time candidate tunings on these trees and keep the fastest.
+ * Starting from the tuning in force, it sweeps one field at a time over its
+ * choices (the others held at the best found so far); each candidate is timed
+ * as `repeats` batched builds of the trees (CUDA events on `stream`) after
+ * one untimed build. The fastest is installed (kdt_set_tuning) and returned in
+ * *best, its time per build in *best_ms (host, may be NULL). Arguments as
+ * kdt_build_batched (the trees' outputs are overwritten; workspace NULL:
+ * allocated once for all candidates and freed). repeats: 1..100.
+ * Errors: those of kdt_build_batched; KDT_ERR_INVALID_ARG (best NULL,
+ * repeats out of range). On an error the tuning in force is unchanged.
+ */
+kdt_status kdt_autotune(const kdt_tree_desc *trees, int32_t num_trees, void *workspace, size_t workspace_bytes,
+                        int32_t repeats, kdt_tuning *best, float *best_ms, void *stream);
+
 /* ---- tracing ------------------------------------------------------------
  * Every kernel launch of the library is counted. With tracing enabled, each
  * launch is also bracketed by two CUDA events recorded on its stream;

@@ -130,7 +130,7 @@ StepPlan plan_step(const StepNeeds& needs) {
   s.max_tiles = (uint32_t)std::min<uint64_t>(needs.points / kTile + needs.maxB + 1, clamp);
   s.nseg_cap = (uint32_t)std::min<uint64_t>(needs.nseg, clamp);
   s.off_cap = (uint32_t)std::min<uint64_t>(needs.nseg + needs.maxB, clamp);
-  s.bigseg_cap = (uint32_t)std::min<uint64_t>(needs.points / (kSelSmallMax + 1) + 1, clamp);
+  s.bigseg_cap = (uint32_t)std::min<uint64_t>(needs.points / (kSelWarpMin + 1) + 1, clamp);
   const int sms = device_sms();
   s.grid_sub = (uint32_t)(sms > 0 ? sms : 148) * (uint32_t)kSubtreeCtasPerSm;
   const uint32_t mt = std::max<uint32_t>(needs.max_trees, 1);
@@ -351,10 +351,14 @@ kdt_status Engine::tick() {
             ? plan_.max_tiles
             : (uint32_t)std::min<uint64_t>(big_points_ / (uint64_t)kTile + (uint64_t)big_count_ + 1,
                                            (uint64_t)plan_.max_tiles);
+    const SelectTuning tune = current_tuning();
+    s_.tiny_max = tune.tiny_max;
+    s_.bitonic_max = tune.bitonic_max;
+    s_.warp_max = tune.warp_max;
     launch_big_step(trees_, s_, tiles_bound, (uint32_t)nseg_bound, plan_.bigseg_cap, has_roots, root_dims_,
                     plan_.needs.widest, plan_.needs.max_d,
-                    plan_.needs.min_d == plan_.needs.max_d ? plan_.needs.max_d : 0, big_points_, plan_.grid_sub,
-                    st_);
+                    plan_.needs.min_d == plan_.needs.max_d ? plan_.needs.max_d : 0, tune, big_points_,
+                    plan_.grid_sub, st_);
     ENGINE_TRY(cudaGetLastError());
     root_dims_ = false;
     uint32_t counts[4];

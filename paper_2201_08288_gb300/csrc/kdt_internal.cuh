@@ -30,7 +30,8 @@ constexpr int kMaxLevels = 30;        // depth / max_levels <= 30
 constexpr int kTile = 2048;           // points per tile of the multi-CTA pipeline
 constexpr int kTileThreads = 256;     // threads of the tile kernels
 constexpr int kSelTinyMax = 32;       // segments up to this size: one thread per segment
-constexpr int kSelSmallMax = 4096;    // segments up to this size: one warp per segment
+constexpr int kSelSmallMax = 4096;    // largest warp-select segment (kdt_tuning warp_max)
+constexpr int kSelWarpMin = 1024;     // smallest warp_max: sizes the list of CTA-select segments
 constexpr int kSubtreeThreads = 256;  // threads of a CTA of the in-shared-memory subtree kernel
 constexpr int kSubtreeWarps = kSubtreeThreads / 32;
 
@@ -155,6 +156,10 @@ struct StepDev {
   uint32_t* off_used;         // device word: words of off_next handed out
   uint32_t off_cap;
   uint32_t bigseg_cap;
+  // select paths by segment size (kdt_tuning): one thread up to tiny_max keys,
+  // a warp's bitonic network up to bitonic_max, a warp's radix select up to
+  // warp_max, a CTA above
+  uint32_t tiny_max, bitonic_max, warp_max;
   uint32_t midseg_cap;
   uint32_t pad4;
   uint2* crow;                // [ncells][2] (slot, row of off_next) of each big child; (kNoRow, slot in

@@ -58,10 +58,18 @@ inline int subtree_capacity(int d) {
   return lo & ~31;
 }
 
+// The tuning of the select paths (kdt_tuning, validated) in force when a level
+// step starts.
+struct SelectTuning {
+  uint32_t tiny_max, bitonic_max, warp_max;
+  int cta_threads, digit_bits;
+};
+SelectTuning current_tuning();
+
 cudaError_t prepare_step_kernels();
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
                      uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d, int uniform_d,
-                     uint64_t points, uint32_t sms, cudaStream_t st);
+                     const SelectTuning& tune, uint64_t points, uint32_t sms, cudaStream_t st);
 
 // Dynamic shared memory of the staged scatter (two CTAs per SM).
 constexpr uint32_t kScatterSmemBytes = 100 * 1024;

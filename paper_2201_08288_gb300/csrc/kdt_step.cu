@@ -452,10 +452,10 @@ __global__ void k_segs(const TreeDev* trees, StepDev s) {
     const uint32_t w = b >= a ? b - a : 0u;
     s.seg_key[g0 + j] = kc + a;
     s.seg_w[g0 + j] = w;
-    if (w > (uint32_t)kSelSmallMax) {
+    if (w > s.warp_max) {
       const uint32_t k = atomicAdd(s.bigseg_count, 1u);
       if (k < s.bigseg_cap) s.bigseg[k] = g0 + j; else set_status(t, ST_INTERNAL);
-    } else if (w > (uint32_t)kSelTinyMax) {
+    } else if (w > s.tiny_max) {
       const uint32_t k = atomicAdd(s.midseg_count, 1u);
       if (k < s.midseg_cap) s.midseg[k] = g0 + j; else set_status(t, ST_INTERNAL);
     }
@@ -497,13 +497,13 @@ __device__ __forceinline__ uint32_t thread_lower_median(const uint32_t* keys, ui
   return med;
 }
 
-// One thread per segment of at most kSelTinyMax points (threads stride over
+// One thread per segment of at most tiny_max <= kSelTinyMax points (threads stride over
 // the segments of the step).
 __global__ void __launch_bounds__(256) k_select_tiny(const TreeDev* trees, StepDev s) {
   const uint32_t nseg = s.seg_base[s.ncells];
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nseg; g += gridDim.x * blockDim.x) {
     const uint32_t w = s.seg_w[g];
-    if (w == 0 || w > (uint32_t)kSelTinyMax) continue;
+    if (w == 0 || w > s.tiny_max) continue;
     const uint32_t* keys = s.seg_key[g];
     uint32_t med;
     if (w <= 8)
@@ -636,9 +636,10 @@ __device__ uint32_t warp_select_stream(const uint32_t* keys, uint32_t w, uint32_
   return st.prefix;
 }
 
-// One warp per listed segment of kSelTinyMax+1 .. kSelSmallMax points: up to
-// 256 keys sorted in registers; up to 1024 keys staged once in shared memory
-// for a radix select; larger segments read from global memory on every pass.
+// One warp per listed segment of tiny_max+1 .. warp_max points: up to
+// bitonic_max keys sorted in registers; up to 1024 keys staged once in shared
+// memory for a radix select; larger segments read from global memory on every
+// pass.
 __global__ void __launch_bounds__(256) k_select_small(const TreeDev* trees, StepDev s) {
   __shared__ uint32_t hist[8][256];
   __shared__ uint32_t stage[8][1024];
@@ -649,11 +650,11 @@ __global__ void __launch_bounds__(256) k_select_small(const TreeDev* trees, Step
     const uint32_t w = s.seg_w[g];
     const uint32_t* keys = s.seg_key[g];
     uint32_t med;
-    if (w <= 64u) {
+    if (w <= s.bitonic_max && w <= 64u) {
       med = warp_bitonic_median<2>(keys, w);
-    } else if (w <= 128u) {
+    } else if (w <= s.bitonic_max && w <= 128u) {
       med = warp_bitonic_median<4>(keys, w);
-    } else if (w <= 256u) {
+    } else if (w <= s.bitonic_max) {
       med = warp_bitonic_median<8>(keys, w);
     } else if (w <= 1024u) {
       uint32_t* st = stage[warp];
@@ -680,17 +681,25 @@ __global__ void __launch_bounds__(256) k_select_small(const TreeDev* trees, Step
   }
 }
 
-// CTAs stride over the listed segments above kSelSmallMax points: 8-bit MSD
-// radix select, keys read from global memory 16 bytes at a time (the
-// unaligned head and tail of the segment by single words), counted into one
-// histogram per warp (the top digits of clustered data fall into few bins),
-// which are summed bin by bin before the digit is chosen.
-__global__ void __launch_bounds__(256) k_select_big(const TreeDev* trees, StepDev s) {
-  constexpr int kW = 8;
-  __shared__ uint32_t hist[kW][256];
-  __shared__ uint32_t tot[256];
+// CTAs of kThreads stride over the listed segments above the warp-select
+// size: MSD radix select with kBits-bit digits (8: four passes, one histogram
+// per warp, which suits the few bins that the top digits of clustered data
+// fall into; 11: three passes over a CTA-wide 2048-bin histogram), keys read
+// from global memory 16 bytes at a time (the unaligned head and tail of the
+// segment by single words).
+template <int kThreads, int kBits>
+__global__ void __launch_bounds__(kThreads) k_select_big(const TreeDev* trees, StepDev s) {
+  constexpr int kW = kThreads / 32;
+  constexpr bool kWarpHist = kBits == 8;
+  constexpr int kBins = 1 << kBits;
+  constexpr int kHist = kWarpHist ? kW * kBins : kBins;
+  constexpr int kPer = kBins >= kThreads ? kBins / kThreads : 1;  // bins per thread in the digit search
+  __shared__ uint32_t hist[kHist];
+  __shared__ uint32_t tot_w[kWarpHist ? kBins : 1];
+  __shared__ uint32_t tmp[33];
   __shared__ uint32_t bcast[2];
   const int warp = threadIdx.x >> 5;
+  uint32_t* tot = kWarpHist ? tot_w : hist;
   const uint32_t cnt = min(*s.bigseg_count, s.bigseg_cap);
   for (uint32_t jb = blockIdx.x; jb < cnt; jb += gridDim.x) {
     const uint32_t g = s.bigseg[jb];
@@ -699,20 +708,22 @@ __global__ void __launch_bounds__(256) k_select_big(const TreeDev* trees, StepDe
     const uint32_t head = min(w, (4u - (uint32_t)(((uintptr_t)keys >> 2) & 3u)) & 3u);
     const uint4* kv = (const uint4*)(keys + head);  // 16-byte aligned
     const uint32_t nv = (w - head) >> 2, tail0 = head + nv * 4u;
-    uint32_t rank = (w - 1) / 2, prefix = 0, mask = 0;
-    for (int shift = 24; shift >= 0; shift -= 8) {
-      for (int i = threadIdx.x; i < kW * 256; i += blockDim.x) (&hist[0][0])[i] = 0;
+    uint32_t rank = (w - 1) / 2, prefix = 0;
+    for (int top = 32; top > 0;) {  // bits [top, 32) are known
+      const int bits = top < kBits ? top : kBits, shift = top - bits;
+      const uint32_t mask = top == 32 ? 0u : ~((1u << top) - 1u), nb = 1u << bits;
+      for (int i = threadIdx.x; i < kHist; i += kThreads) hist[i] = 0;
       __syncthreads();
-      uint32_t* wh = hist[warp];
+      uint32_t* wh = kWarpHist ? hist + warp * kBins : hist;
       auto add = [&](uint32_t u) {
         const uint32_t k = ord_key(__uint_as_float(u));
-        if ((k & mask) == prefix) atomicAdd(&wh[(k >> shift) & 255u], 1u);
+        if ((k & mask) == prefix) atomicAdd(&wh[(k >> shift) & (nb - 1u)], 1u);
       };
       uint32_t v = threadIdx.x;
-      for (; v + 3 * 256 < nv; v += 4 * 256) {
+      for (; v + 3 * kThreads < nv; v += 4 * kThreads) {
         uint4 q[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = __ldg(kv + v + u * 256);
+        for (int u = 0; u < 4; ++u) q[u] = __ldg(kv + v + u * kThreads);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           add(q[u].x);
@@ -721,7 +732,7 @@ __global__ void __launch_bounds__(256) k_select_big(const TreeDev* trees, StepDe
           add(q[u].w);
         }
       }
-      for (; v < nv; v += 256) {
+      for (; v < nv; v += kThreads) {
         const uint4 q = __ldg(kv + v);
         add(q.x);
         add(q.y);
@@ -731,28 +742,44 @@ __global__ void __launch_bounds__(256) k_select_big(const TreeDev* trees, StepDe
       if (threadIdx.x < head) add(__ldg(keys + threadIdx.x));
       if (threadIdx.x < w - tail0) add(__ldg(keys + tail0 + threadIdx.x));
       __syncthreads();
-      {
-        uint32_t sum = 0;
+      if (kWarpHist) {
+        for (int b = threadIdx.x; b < kBins; b += kThreads) {
+          uint32_t sum = 0;
 #pragma unroll
-        for (int q = 0; q < kW; ++q) sum += hist[q][threadIdx.x];
-        tot[threadIdx.x] = sum;
+          for (int q = 0; q < kW; ++q) sum += hist[q * kBins + b];
+          tot[b] = sum;
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      if (threadIdx.x < 32) {
-        uint32_t below;
-        const uint32_t digit = warp_find_digit(tot, rank, &below);
-        if (threadIdx.x == 0) {
-          bcast[0] = digit;
-          bcast[1] = below;
+      // the bin holding `rank`: each thread scans kPer consecutive bins
+      const uint32_t first = (uint32_t)threadIdx.x * kPer;
+      uint32_t loc[kPer], sum = 0;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        loc[q] = first + q < nb ? tot[first + q] : 0u;
+        sum += loc[q];
+      }
+      uint32_t all;
+      const uint32_t ex = block_excl_scan(sum, tmp, &all);
+      if (rank >= ex && rank < ex + sum) {
+        uint32_t acc = ex;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+          if (rank < acc + loc[q]) {
+            bcast[0] = first + q;
+            bcast[1] = acc;
+            break;
+          }
+          acc += loc[q];
         }
       }
       __syncthreads();
       rank -= bcast[1];
       prefix |= bcast[0] << shift;
-      mask |= 255u << shift;
+      top = shift;
+      __syncthreads();
     }
     if (threadIdx.x == 0) s.seg_med[g] = prefix;
-    __syncthreads();
   }
 }
 
@@ -1011,7 +1038,7 @@ cudaError_t prepare_step_kernels() {
 
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
                      uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d, int uniform_d,
-                     uint64_t points, uint32_t sms, cudaStream_t st) {
+                     const SelectTuning& tune, uint64_t points, uint32_t sms, cudaStream_t st) {
   const uint32_t nc = s.ncells;
   if (nc == 0) return;
   { TraceScope ts(K_PREP, st); k_prep<<<1, 1024, 0, st>>>(trees, s); }
@@ -1036,7 +1063,18 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
   }
   if (max_bigseg) {
     TraceScope ts(K_SELECT_BIG, st);
-    k_select_big<<<std::max<uint32_t>(1, std::min<uint32_t>(max_bigseg, sms * 4u)), 256, 0, st>>>(trees, s);
+    const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>(max_bigseg, sms * 4u));
+    if (tune.cta_threads == 512) {
+      if (tune.digit_bits == 8)
+        k_select_big<512, 8><<<grid, 512, 0, st>>>(trees, s);
+      else
+        k_select_big<512, 11><<<grid, 512, 0, st>>>(trees, s);
+    } else {
+      if (tune.digit_bits == 8)
+        k_select_big<256, 8><<<grid, 256, 0, st>>>(trees, s);
+      else
+        k_select_big<256, 11><<<grid, 256, 0, st>>>(trees, s);
+    }
   }
   // a CTA per cell while cells are few (large subset counts, deep scans),
   // a warp per cell once they are many

@@ -34,7 +34,7 @@ EXPORTED = ["kdt_workspace_size", "kdt_build", "kdt_workspace_size_host", "kdt_b
             "kdt_subtree_capacity", "kdt_status_str", "kdt_trace_enable", "kdt_launch_count",
             "kdt_trace_read", "kdt_build_noalloc", "kdt_workspace_size_batched", "kdt_build_batched",
             "kdt_server_create", "kdt_server_submit", "kdt_server_poll", "kdt_server_stats",
-            "kdt_server_destroy"]
+            "kdt_server_destroy", "kdt_tuning_default", "kdt_set_tuning", "kdt_get_tuning", "kdt_autotune"]
 
 
 class KdtError(RuntimeError):
@@ -79,6 +79,17 @@ class kdt_server_info(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("ticks", ctypes.c_uint64), ("in_flight", ctypes.c_int32), ("peak_in_flight", ctypes.c_int32),
                 ("arena_bytes", ctypes.c_uint64), ("arena_bytes_in_use", ctypes.c_uint64)]
+
+
+class kdt_tuning(ctypes.Structure):
+    _fields_ = [("tiny_max", ctypes.c_int32), ("bitonic_max", ctypes.c_int32), ("warp_max", ctypes.c_int32),
+                ("cta_threads", ctypes.c_int32), ("digit_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+TUNING_FIELDS = ("tiny_max", "bitonic_max", "warp_max", "cta_threads", "digit_bits")
+# the choices kdt_set_tuning accepts, per field
+TUNING_CHOICES = {"tiny_max": (8, 16, 32), "bitonic_max": (64, 128, 256), "warp_max": (1024, 2048, 4096),
+                  "cta_threads": (256, 512), "digit_bits": (8, 11)}
 
 
 _lib = None
@@ -131,6 +142,15 @@ def load_library(path: str = LIB_PATH):
     lib.kdt_launch_count.restype = ctypes.c_uint64
     lib.kdt_trace_read.argtypes = [ctypes.POINTER(kdt_kernel_stat), ctypes.c_int32, ctypes.c_int32]
     lib.kdt_trace_read.restype = ctypes.c_int32
+    T = ctypes.POINTER(kdt_tuning)
+    lib.kdt_tuning_default.argtypes = [T]
+    lib.kdt_tuning_default.restype = None
+    lib.kdt_set_tuning.argtypes = [T]
+    lib.kdt_set_tuning.restype = ctypes.c_int
+    lib.kdt_get_tuning.argtypes = [T]
+    lib.kdt_get_tuning.restype = ctypes.c_int
+    lib.kdt_autotune.argtypes = [D, ctypes.c_int32, vp, sz, ctypes.c_int32, T, ctypes.POINTER(ctypes.c_float), vp]
+    lib.kdt_autotune.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -387,6 +407,58 @@ def kdt_build_batched(items, *, workspace=None, stream=None, outputs=None, descs
         o = outs[i]
         trees.append(Tree(o.perm[:n], o.split_vals[:m], o.split_dims[:m], o.node_offsets[:(1 << L) + 1], L))
     return trees, [int(stats[i]) for i in range(num)]
+
+
+def _tuning_dict(t: kdt_tuning) -> dict:
+    return {f: int(getattr(t, f)) for f in TUNING_FIELDS}
+
+
+def tuning_default() -> dict:
+    """The library's default tuning of the select paths (kdt_tuning_default)."""
+    t = kdt_tuning()
+    load_library().kdt_tuning_default(ctypes.byref(t))
+    return _tuning_dict(t)
+
+
+def get_tuning() -> dict:
+    """The tuning in force (kdt_get_tuning)."""
+    t = kdt_tuning()
+    st = load_library().kdt_get_tuning(ctypes.byref(t))
+    if st:
+        raise KdtError(st, "kdt_get_tuning")
+    return _tuning_dict(t)
+
+
+def set_tuning(tuning=None) -> None:
+    """Install a tuning (dict of TUNING_FIELDS; None: the defaults)."""
+    lib = load_library()
+    if tuning is None:
+        st = lib.kdt_set_tuning(None)
+    else:
+        t = kdt_tuning(**{f: int(tuning[f]) for f in TUNING_FIELDS})
+        st = lib.kdt_set_tuning(ctypes.byref(t))
+    if st:
+        raise KdtError(st, "kdt_set_tuning")
+
+
+def autotune(items, *, repeats: int = 2, workspace=None, stream=None, outputs=None):
+    """Time candidate tunings on these trees (items as for kdt_build_batched),
+    install the fastest and return (tuning dict, ms per build)."""
+    import torch
+    descs, outs = make_descs(items, outputs)
+    ws_ptr, ws_bytes = 0, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    best = kdt_tuning()
+    ms = ctypes.c_float()
+    st = load_library().kdt_autotune(descs, len(descs), ws_ptr or None, ws_bytes, repeats, ctypes.byref(best),
+                                     ctypes.byref(ms), stream.cuda_stream)
+    if st:
+        raise KdtError(st, "kdt_autotune")
+    del outs
+    return _tuning_dict(best), float(ms.value)
 
 
 class Server:

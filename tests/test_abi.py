@@ -68,3 +68,45 @@ def test_invalid_params_rejected_on_host(lib, kw):
     with pytest.raises(kdt.KdtError) as e:
         kdt.kdt_workspace_size(p)
     assert e.value.status == 1
+
+
+def test_tuning_struct_layout_matches_header():
+    from paper_2201_08288_gb300 import kdt
+    src = open(os.path.join(ROOT, "include", "kdt.h")).read()
+    body = re.search(r"typedef struct kdt_tuning \{(.*?)\} kdt_tuning;", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\s([a-z0-9_]+)(?:\[\d+\])?\s*;", body)
+    assert fields == [f[0] for f in kdt.kdt_tuning._fields_]
+    assert ctypes.sizeof(kdt.kdt_tuning) == 32
+
+
+def test_tuning_set_get_and_validation_need_no_gpu(lib):
+    """The tuning is host state: defaults, a round trip through every choice of
+    every field, and rejection of anything else (the tuning in force kept)."""
+    from paper_2201_08288_gb300 import kdt
+    d = kdt.tuning_default()
+    assert d == {"tiny_max": 32, "bitonic_max": 256, "warp_max": 4096, "cta_threads": 256, "digit_bits": 11}
+    kdt.set_tuning(None)
+    assert kdt.get_tuning() == d
+    try:
+        for f, choices in kdt.TUNING_CHOICES.items():
+            for v in choices:
+                t = dict(d)
+                t[f] = v
+                kdt.set_tuning(t)
+                assert kdt.get_tuning() == t
+        kept = kdt.get_tuning()
+        for f, bad in [("tiny_max", 0), ("tiny_max", 64), ("bitonic_max", 32), ("warp_max", 8192),
+                       ("cta_threads", 128), ("digit_bits", 4)]:
+            t = dict(d)
+            t[f] = bad
+            with pytest.raises(kdt.KdtError) as e:
+                kdt.set_tuning(t)
+            assert e.value.status == 1
+            assert kdt.get_tuning() == kept
+        raw = kdt.kdt_tuning(**d)
+        raw.reserved[1] = 7
+        assert lib.kdt_set_tuning(ctypes.byref(raw)) == 1
+        assert lib.kdt_get_tuning(None) == 1
+    finally:
+        kdt.set_tuning(None)
