@@ -142,8 +142,10 @@ kdt_status kdt_build_host(const float *points_host, const kdt_params *p, void *w
  * Many independent trees (different n, d, r, rules) built together: every
  * level step runs once over the cells of all trees (each tree at its own
  * level), and every cell that fits in shared memory is finished by one
- * persistent launch per step. Each tree's outputs equal its kdt_build outputs
- * bit for bit. */
+ * persistent launch per step. After the roots' step, all steps run as one
+ * CUDA graph launch: a conditional while node repeats a recorded pair of
+ * steps that read their cell counts on the device, until no cell is left.
+ * Each tree's outputs equal its kdt_build outputs bit for bit. */
 typedef struct kdt_tree_desc {
   const float *points;         /* device, float32 SoA [d][n] (as kdt_build)              */
   kdt_params params;           /* per tree; explicit subset ids are device pointers      */

@@ -5,6 +5,7 @@
 // segment knows its tree) and finishes every cell that became small in one
 // persistent subtree launch. Results per tree are identical to kdt_build's:
 // no reduction crosses trees.
+#include <cstdlib>
 #include <algorithm>
 #include <vector>
 
@@ -96,7 +97,13 @@ kdt_status kdt_build_batched(const kdt_tree_desc* trees, int32_t num_trees, void
                   trees[i].out_node_offsets);
     }
     if (s != KDT_OK) break;
-    if ((s = e.run_to_completion()) != KDT_OK) break;
+    // all level steps after the roots' in one graph launch (KDT_BATCH_GRAPH=0:
+    // every step launched and sized by the host, a debugging aid)
+    static const bool use_graph = [] {
+      const char* v = std::getenv("KDT_BATCH_GRAPH");
+      return !(v && v[0] == '0');
+    }();
+    if ((s = use_graph ? e.run_graph() : e.run_to_completion()) != KDT_OK) break;
     s = e.finalize(slots, &status, &levels);
   } while (0);
   if (owned) {

@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "kdt_engine.h"
+#include "kdt_trace.h"
 
 namespace kdt {
 
@@ -14,7 +15,14 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // Engine words.
-enum Word { W_NTILES = 0, W_BIGSEG, W_HEAD, W_NEXTBIG, W_SMALL, W_BIGPTS, W_SMALLPTS, W_OFFUSED, W_MIDSEG, W_COUNT };
+// W_NC0, W_NC1, W_ITERS (adjacent): the cell counts of the two lists and the
+// iteration count of a graph-driven run
+enum Word {
+  W_NTILES = 0, W_BIGSEG, W_HEAD, W_NEXTBIG, W_SMALL, W_BIGPTS, W_SMALLPTS, W_OFFUSED, W_MIDSEG,
+  W_NC0, W_NC1, W_ITERS, W_COUNT
+};
+// a graph-driven run's iterations (two level steps each) before it gives up
+constexpr uint32_t kGraphIterMax = KDT_MAX_LEVELS + 4;
 // Per-slot words: [which][max_trees].
 enum SlotWord { S_TERM = 0, S_STATUS, S_LEVELS, S_LIVE, S_COUNT };
 
@@ -382,7 +390,7 @@ kdt_status Engine::tick() {
     big_points_ = 0;
   }
   if (small_count_ > 0) {
-    launch_subtree(trees_, small_, small_count_, words_ + W_HEAD, slices_, plan_.needs.slice_cells,
+    launch_subtree(trees_, small_, small_count_, nullptr, words_ + W_HEAD, slices_, plan_.needs.slice_cells,
                    std::min(plan_.grid_sub, small_count_), small_points_, st_);
     ENGINE_TRY(cudaGetLastError());
     small_count_ = 0;
@@ -465,6 +473,114 @@ kdt_status Engine::finalize(const std::vector<uint32_t>& slots, std::vector<kdt_
     (*status)[i] = map_status(st[slots[i]]);
     (*levels)[i] = lv[slots[i]];
   }
+  return KDT_OK;
+}
+
+kdt_status Engine::record_tick(int p) {
+  // the counters a step appends to start from zero
+  ENGINE_TRY(cudaMemsetAsync(words_ + W_NC0 + (p ^ 1), 0, 4, st_));
+  ENGINE_TRY(cudaMemsetAsync(words_ + W_BIGPTS, 0, 4, st_));
+  ENGINE_TRY(cudaMemsetAsync(words_ + W_OFFUSED, 0, 4, st_));
+  ENGINE_TRY(cudaMemsetAsync(words_ + W_SMALL, 0, 4, st_));
+  ENGINE_TRY(cudaMemsetAsync(words_ + W_SMALLPTS, 0, 4, st_));
+  StepDev sd = s_;
+  sd.cells = big_[p];
+  sd.ncells = plan_.maxB;  // a capacity: the count is the device word
+  sd.ncells_dev = words_ + W_NC0 + p;
+  sd.next_big = big_[p ^ 1];
+  sd.next_big_count = words_ + W_NC0 + (p ^ 1);
+  sd.off_cur = off_[p];
+  sd.obase_cur = obase_[p];
+  sd.off_next = off_[p ^ 1];
+  sd.obase_next = obase_[p ^ 1];
+  const SelectTuning tune = current_tuning();
+  sd.tiny_max = tune.tiny_max;
+  sd.bitonic_max = tune.bitonic_max;
+  sd.warp_max = tune.warp_max;
+  launch_big_step(trees_, sd, plan_.max_tiles, plan_.nseg_cap, plan_.bigseg_cap, false, false, plan_.needs.widest,
+                  plan_.needs.max_d, plan_.needs.min_d == plan_.needs.max_d ? plan_.needs.max_d : 0, tune, 0,
+                  plan_.grid_sub, st_);
+  ENGINE_TRY(cudaGetLastError());
+  launch_subtree(trees_, small_, plan_.cap_small, words_ + W_SMALL, words_ + W_HEAD, slices_,
+                 plan_.needs.slice_cells, plan_.grid_sub, 0, st_);
+  ENGINE_TRY(cudaGetLastError());
+  return KDT_OK;
+}
+
+kdt_status Engine::run_graph() {
+  // the roots' step (presort, root dims) is sized and launched by the host
+  if (!pending_big_.empty() || !pending_small_.empty()) {
+    const kdt_status s = tick();
+    if (s != KDT_OK) return s;
+  }
+  if (!busy()) return KDT_OK;
+  // every later step runs inside one graph launch: a while loop whose body is
+  // a step over list p0 then one over list p0 ^ 1, each reading its count
+  // from the device, until a step leaves no cell (the tick above has
+  // launched the subtree kernel over its queue, so that queue is empty)
+  const int p0 = cur_;
+  uint32_t init[3] = {0u, 0u, 0u};  // W_NC0, W_NC1, W_ITERS
+  init[p0] = big_count_;
+  ENGINE_TRY(cudaMemcpyAsync(words_ + W_NC0, init, sizeof(init), cudaMemcpyHostToDevice, st_));
+  ENGINE_TRY(cudaStreamSynchronize(st_));
+  // the steps are recorded on a private stream (the caller's may be the
+  // legacy default stream, which cannot be captured); the graph runs on the
+  // caller's stream
+  struct Graphs {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaStream_t cs = nullptr;
+    ~Graphs() {
+      if (ex) cudaGraphExecDestroy(ex);
+      if (g) cudaGraphDestroy(g);
+      if (cs) cudaStreamDestroy(cs);
+    }
+  } gr;
+  auto fail = [&](const char* what, cudaError_t e) {
+    (void)cudaGetLastError();
+    if (debug_) std::fprintf(stderr, "kdt graph run: %s: %s\n", what, cudaGetErrorString(e));
+    return KDT_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&gr.cs, cudaStreamNonBlocking)) != cudaSuccess) return fail("stream", e);
+  if ((e = cudaGraphCreate(&gr.g, 0)) != cudaSuccess) return fail("graph", e);
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, gr.g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+    return fail("conditional handle", e);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop;
+  if ((e = cudaGraphAddNode(&loop, gr.g, nullptr, nullptr, 0, &cp)) != cudaSuccess) return fail("while node", e);
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(gr.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess)
+    return fail("begin capture", e);
+  const cudaStream_t caller = st_;
+  st_ = gr.cs;
+  const uint64_t l0 = kdt_launch_count();
+  kdt_status rec = record_tick(p0);
+  if (rec == KDT_OK) rec = record_tick(p0 ^ 1);
+  if (rec == KDT_OK) launch_loop_cond(h, words_ + W_NC0 + p0, words_ + W_ITERS, kGraphIterMax, st_);
+  const uint64_t per_iter = kdt_launch_count() - l0;
+  st_ = caller;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(gr.cs, &captured);
+  if (rec != KDT_OK) return rec;
+  if (ce != cudaSuccess) return fail("end capture", ce);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail("recording", e);
+  if ((e = cudaGraphInstantiate(&gr.ex, gr.g, 0)) != cudaSuccess) return fail("instantiate", e);
+  if ((e = cudaGraphLaunch(gr.ex, st_)) != cudaSuccess) return fail("launch", e);
+  uint32_t fin[3];
+  ENGINE_TRY(cudaMemcpyAsync(fin, words_ + W_NC0, sizeof(fin), cudaMemcpyDeviceToHost, st_));
+  ENGINE_TRY(cudaStreamSynchronize(st_));
+  if (fin[2] > 1) trace_add_launches((uint64_t)(fin[2] - 1) * per_iter);  // replays beyond the recorded one
+  graph_iters_ = fin[2];
+  if (fin[p0] != 0) return KDT_ERR_CUDA;  // stopped at the iteration cap with cells left
+  big_count_ = small_count_ = 0;
+  big_points_ = small_points_ = 0;
   return KDT_OK;
 }
 

@@ -80,6 +80,12 @@ class Engine {
                       std::vector<int32_t>* levels);
   // Run ticks until nothing is left in flight.
   kdt_status run_to_completion();
+  // The same with one graph launch: the first tick (new roots) from the
+  // host, then every later tick inside a CUDA graph whose conditional while
+  // node repeats a pair of recorded ticks until no cell is left.
+  kdt_status run_graph();
+  // Iterations (pairs of ticks) of the last run_graph.
+  uint32_t graph_iters() const { return graph_iters_; }
 
  private:
   StepPlan plan_;
@@ -100,6 +106,9 @@ class Engine {
   uint64_t big_points_ = 0, small_points_ = 0;
   bool root_dims_ = false;
   bool debug_ = false;
+  uint32_t graph_iters_ = 0;
+  // Record a tick over cell list p into the stream's capture (counts on the device).
+  kdt_status record_tick(int p);
   std::vector<Cell> pending_big_, pending_small_;
   std::vector<TreeHost> host_;       // per slot: leaf-sort view of a presorted tree
   std::vector<uint8_t> leafsort_;    // per slot

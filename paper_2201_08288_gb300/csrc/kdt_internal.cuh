@@ -117,7 +117,8 @@ struct TermRec {
 // (cell, subset) segment).
 struct StepDev {
   const Cell* cells;      // big cells of this step
-  uint32_t ncells;
+  uint32_t ncells;              // cells of this step (steps driven by the host)
+  const uint32_t* ncells_dev;   // if set: the device word that holds it (steps inside a graph)
   uint32_t pad;
   uint32_t* tile_base;    // [ncells+1] first tile of each cell (exclusive scan)
   uint32_t* seg_base;     // [ncells+1] first segment of each cell
@@ -239,6 +240,12 @@ __device__ __forceinline__ uint32_t subset_at(const TreeDev& t, int level, int64
 
 // Terminal test for a cell about to be processed at `level` (reading R8 in
 // leaf mode; empty cells and the last level in depth mode).
+// Cells of a step: the host's count, or the device word a graph-driven step
+// reads (clamped to the capacity of the cell lists).
+__device__ __forceinline__ uint32_t ncells_of(const StepDev& s) {
+  return s.ncells_dev ? min(*s.ncells_dev, s.next_big_cap) : s.ncells;
+}
+
 __device__ __forceinline__ bool is_terminal(const TreeDev& t, uint32_t count, int level, int stall) {
   if (t.depth > 0) return count == 0 || level >= t.depth;
   return count <= (uint32_t)t.leaf_size || stall >= t.stall_limit;

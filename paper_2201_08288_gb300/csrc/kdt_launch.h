@@ -67,6 +67,11 @@ struct SelectTuning {
 SelectTuning current_tuning();
 
 cudaError_t prepare_step_kernels();
+// One thread: the loop condition of a graph whose body is a pair of level
+// steps (keep going while ncells_next > 0, at most `limit` iterations; the
+// count of iterations is kept in *iters).
+void launch_loop_cond(cudaGraphConditionalHandle h, const uint32_t* ncells_next, uint32_t* iters, uint32_t limit,
+                      cudaStream_t st);
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
                      uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d, int uniform_d,
                      const SelectTuning& tune, uint64_t points, uint32_t sms, cudaStream_t st);
@@ -80,8 +85,11 @@ void launch_scatter(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, 
                     uint64_t points, int uniform_d, cudaStream_t st);
 
 cudaError_t prepare_subtree_kernel();
-void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head, LCell* slices,
-                    uint32_t slice_cells, uint32_t grid, uint64_t points, cudaStream_t st);
+// count_dev: if set, the device word holding the queue's length (count is
+// then its cap)
+void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t* count_dev,
+                    uint32_t* head, LCell* slices, uint32_t slice_cells, uint32_t grid, uint64_t points,
+                    cudaStream_t st);
 
 void launch_iota(uint32_t* out, uint32_t n, cudaStream_t st);
 

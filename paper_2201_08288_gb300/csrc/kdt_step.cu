@@ -55,10 +55,11 @@ __device__ __forceinline__ bool tile_of(const StepDev& s, uint32_t tile, uint2* 
 __global__ void k_prep(const TreeDev* trees, StepDev s) {
   __shared__ uint32_t tmp[33];
   uint32_t tile_run = 0, seg_run = 0;
-  for (uint32_t c0 = 0; c0 < s.ncells; c0 += blockDim.x) {
+  const uint32_t ncells = ncells_of(s);
+  for (uint32_t c0 = 0; c0 < ncells; c0 += blockDim.x) {
     const uint32_t c = c0 + threadIdx.x;
     uint32_t nt = 0, ns = 0;
-    if (c < s.ncells) {
+    if (c < ncells) {
       const Cell cell = s.cells[c];
       const TreeDev& t = trees[cell.tree];
       nt = (cell.count + kTile - 1) / kTile;
@@ -71,7 +72,7 @@ __global__ void k_prep(const TreeDev* trees, StepDev s) {
     uint32_t tot_t, tot_s;
     const uint32_t et = block_excl_scan(nt, tmp, &tot_t);
     const uint32_t es = block_excl_scan(ns, tmp, &tot_s);
-    if (c < s.ncells) {
+    if (c < ncells) {
       s.tile_base[c] = tile_run + et;
       s.seg_base[c] = seg_run + es;
     }
@@ -79,8 +80,8 @@ __global__ void k_prep(const TreeDev* trees, StepDev s) {
     seg_run += tot_s;
   }
   if (threadIdx.x == 0) {
-    s.tile_base[s.ncells] = tile_run;
-    s.seg_base[s.ncells] = seg_run;
+    s.tile_base[ncells] = tile_run;
+    s.seg_base[ncells] = seg_run;
     *s.ntiles_total = tile_run;
     *s.bigseg_count = 0;
     *s.midseg_count = 0;
@@ -88,8 +89,7 @@ __global__ void k_prep(const TreeDev* trees, StepDev s) {
 }
 
 // One CTA per cell: tile list entries; zeroed subset counts of a presorted root.
-__global__ void k_tiles(const TreeDev* trees, StepDev s) {
-  const uint32_t c = blockIdx.x;
+__device__ __forceinline__ void tiles_cell(const TreeDev* trees, const StepDev& s, uint32_t c) {
   const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
   for (uint32_t j = tb + threadIdx.x; j < te; j += blockDim.x)
     s.tiles[j] = make_uint2(c, (j - tb) * (uint32_t)kTile);
@@ -98,6 +98,14 @@ __global__ void k_tiles(const TreeDev* trees, StepDev s) {
     const TreeDev& t = trees[cell.tree];
     if (t.presorted)
       for (int j = threadIdx.x; j < t.r; j += blockDim.x) t.root_cur[j] = 0;
+  }
+}
+
+__global__ void k_tiles(const TreeDev* trees, StepDev s) {
+  const uint32_t nc = ncells_of(s);
+  for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
+    tiles_cell(trees, s, c);
+    __syncthreads();  // the cell's shared memory is free for the next one
   }
 }
 
@@ -139,9 +147,9 @@ __global__ void __launch_bounds__(kTileThreads) k_ps_count(const TreeDev* trees,
 // exclusive scan of the counts (which also become the fill cursors); subsets
 // by index mod r: r_j = floor(n/r) + [j < n mod r] points each; contiguous
 // subsets (already in order): subset j starts at ceil(j n / r).
-__global__ void k_ps_offsets(const TreeDev* trees, StepDev s) {
+__device__ __forceinline__ void ps_offsets_cell(const TreeDev* trees, const StepDev& s, uint32_t c) {
   __shared__ uint32_t tmp[33];
-  const Cell cell = s.cells[blockIdx.x];
+  const Cell cell = s.cells[c];
   if (cell.level != 0) return;
   const TreeDev& t = trees[cell.tree];
   const uint32_t r = (uint32_t)t.r, n = cell.count;
@@ -168,6 +176,14 @@ __global__ void k_ps_offsets(const TreeDev* trees, StepDev s) {
   } else {
     for (uint32_t j = threadIdx.x; j <= r; j += blockDim.x)
       t.root_off[j] = (uint32_t)(((uint64_t)j * n + r - 1) / r);
+  }
+}
+
+__global__ void k_ps_offsets(const TreeDev* trees, StepDev s) {
+  const uint32_t nc = ncells_of(s);
+  for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
+    ps_offsets_cell(trees, s, c);
+    __syncthreads();  // the cell's shared memory is free for the next one
   }
 }
 
@@ -362,8 +378,7 @@ __device__ __forceinline__ double key_range(uint32_t lo, uint32_t hi) {
 // partials and pick the coordinate of largest range (lowest on ties). Every
 // thread walks its own tiles, eight coordinates at a time (four 16-byte loads
 // per tile: a tile's record holds min, max of each coordinate in turn).
-__global__ void __launch_bounds__(1024) k_pick_dim(const TreeDev* trees, StepDev s) {
-  const uint32_t c = blockIdx.x;
+__device__ __forceinline__ void pick_dim_cell(const TreeDev* trees, const StepDev& s, uint32_t c) {
   const Cell cell = s.cells[c];
   const TreeDev& t = trees[cell.tree];
   if (t.key_rule != KEY_WIDEST || cell.dim >= 0) return;
@@ -422,6 +437,14 @@ __global__ void __launch_bounds__(1024) k_pick_dim(const TreeDev* trees, StepDev
   }
 }
 
+__global__ void __launch_bounds__(1024) k_pick_dim(const TreeDev* trees, StepDev s) {
+  const uint32_t nc = ncells_of(s);
+  for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
+    pick_dim_cell(trees, s, c);
+    __syncthreads();  // the cell's shared memory is free for the next one
+  }
+}
+
 // ------------------------------------------------------------ segments
 
 // Key column of a cell (raw float bits; ord_key is applied on every load).
@@ -437,8 +460,7 @@ __device__ __forceinline__ uint32_t kload(const uint32_t* p) { return ord_key(__
 // lists of segments for the warp and CTA selects. Offsets are clamped to the
 // cell, so a damaged table cannot send a later kernel outside it (it is
 // reported instead).
-__global__ void k_segs(const TreeDev* trees, StepDev s) {
-  const uint32_t c = blockIdx.x;
+__device__ __forceinline__ void segs_cell(const TreeDev* trees, const StepDev& s, uint32_t c) {
   const Cell cell = s.cells[c];
   const TreeDev& t = trees[cell.tree];
   const uint32_t r = (uint32_t)t.r;
@@ -459,6 +481,14 @@ __global__ void k_segs(const TreeDev* trees, StepDev s) {
       const uint32_t k = atomicAdd(s.midseg_count, 1u);
       if (k < s.midseg_cap) s.midseg[k] = g0 + j; else set_status(t, ST_INTERNAL);
     }
+  }
+}
+
+__global__ void k_segs(const TreeDev* trees, StepDev s) {
+  const uint32_t nc = ncells_of(s);
+  for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
+    segs_cell(trees, s, c);
+    __syncthreads();  // the cell's shared memory is free for the next one
   }
 }
 
@@ -500,7 +530,7 @@ __device__ __forceinline__ uint32_t thread_lower_median(const uint32_t* keys, ui
 // One thread per segment of at most tiny_max <= kSelTinyMax points (threads stride over
 // the segments of the step).
 __global__ void __launch_bounds__(256) k_select_tiny(const TreeDev* trees, StepDev s) {
-  const uint32_t nseg = s.seg_base[s.ncells];
+  const uint32_t nseg = s.seg_base[ncells_of(s)];
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nseg; g += gridDim.x * blockDim.x) {
     const uint32_t w = s.seg_w[g];
     if (w == 0 || w > s.tiny_max) continue;
@@ -786,10 +816,9 @@ __global__ void __launch_bounds__(kThreads) k_select_big(const TreeDev* trees, S
 // One CTA per cell: count-weighted lower median of the segment medians: the
 // smallest median m whose segments with median <= m hold at least
 // ceil(W/2) of the W points (weighted 8-bit MSD radix select).
-__global__ void __launch_bounds__(256) k_combine(const TreeDev* trees, StepDev s) {
+__device__ __forceinline__ void combine_cell(const TreeDev* trees, const StepDev& s, uint32_t c) {
   __shared__ uint32_t hist[256];
   __shared__ uint32_t bcast[2];
-  const uint32_t c = blockIdx.x;
   const Cell cell = s.cells[c];
   const TreeDev& t = trees[cell.tree];
   const int r = t.r;
@@ -826,14 +855,20 @@ __global__ void __launch_bounds__(256) k_combine(const TreeDev* trees, StepDev s
   }
 }
 
+__global__ void __launch_bounds__(256) k_combine(const TreeDev* trees, StepDev s) {
+  const uint32_t nc = ncells_of(s);
+  for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
+    combine_cell(trees, s, c);
+    __syncthreads();  // the cell's shared memory is free for the next one
+  }
+}
+
 // One warp per cell (steps with many cells): the same weighted lower median
 // by the warp radix select, which starts at the first bit where the cell's
 // segment medians differ.
-__global__ void __launch_bounds__(256) k_combine_warp(const TreeDev* trees, StepDev s) {
+__device__ __forceinline__ void combine_warp_cell(const TreeDev* trees, const StepDev& s, uint32_t c) {
   __shared__ uint32_t hist[8][256];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t c = blockIdx.x * 8u + (uint32_t)warp;
-  if (c >= s.ncells) return;
   const Cell cell = s.cells[c];
   const TreeDev& t = trees[cell.tree];
   const uint32_t g0 = s.seg_base[c];
@@ -849,14 +884,17 @@ __global__ void __launch_bounds__(256) k_combine_warp(const TreeDev* trees, Step
   }
 }
 
+__global__ void __launch_bounds__(256, 1) k_combine_warp(const TreeDev* trees, StepDev s) {
+  const uint32_t nc = ncells_of(s);
+  for (uint32_t c = blockIdx.x * 8u + (threadIdx.x >> 5); c < nc; c += gridDim.x * 8u) combine_warp_cell(trees, s, c);
+}
+
 // ------------------------------------------------------------ partition
 
 // Per tile: number of points with key <= split. The tile's key range is
 // read 16 bytes at a time (its unaligned head and tail by single words).
-__global__ void __launch_bounds__(kTileThreads) k_part_count(const TreeDev* trees, StepDev s) {
-  uint2 tl;
-  if (!tile_of(s, blockIdx.x, &tl)) return;
-  __shared__ uint32_t red[kWarps];
+__device__ __forceinline__ void part_count_tile(const TreeDev* trees, const StepDev& s, uint32_t tile, uint2 tl,
+                                                uint32_t* red) {
   const Cell cell = s.cells[tl.x];
   const TreeDev& t = trees[cell.tree];
   const float* X = src_cols(t, cell.level) + (int64_t)s.kdim[tl.x] * t.n + cell.begin + tl.y;
@@ -885,14 +923,23 @@ __global__ void __launch_bounds__(kTileThreads) k_part_count(const TreeDev* tree
   if (threadIdx.x == 0) {
     uint32_t tot = 0;
     for (int w = 0; w < kWarps; ++w) tot += red[w];
-    s.tile_left[blockIdx.x] = tot;
+    s.tile_left[tile] = tot;
+  }
+}
+
+// CTAs stride over the tiles (one per CTA when the grid covers them).
+__global__ void __launch_bounds__(kTileThreads) k_part_count(const TreeDev* trees, StepDev s) {
+  __shared__ uint32_t red[kWarps];
+  const uint32_t ntiles = *s.ntiles_total;
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    part_count_tile(trees, s, tile, s.tiles[tile], red);
+    __syncthreads();  // red is reused by the next tile
   }
 }
 
 // One CTA per cell: exclusive scan of its tiles' left counts.
-__global__ void k_part_scan(StepDev s) {
+__device__ __forceinline__ void part_scan_cell(const StepDev& s, uint32_t c) {
   __shared__ uint32_t tmp[33];
-  const uint32_t c = blockIdx.x;
   const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
   uint32_t run = 0;
   for (uint32_t j0 = tb; j0 < te; j0 += blockDim.x) {
@@ -906,11 +953,17 @@ __global__ void k_part_scan(StepDev s) {
   if (threadIdx.x == 0) s.lcount[c] = run;
 }
 
+__global__ void k_part_scan(StepDev s) {
+  const uint32_t nc = ncells_of(s);
+  for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
+    part_scan_cell(s, c);
+    __syncthreads();  // the cell's shared memory is free for the next one
+  }
+}
+
 // One warp per cell (steps with many cells, few tiles each).
-__global__ void __launch_bounds__(256) k_part_scan_warp(StepDev s) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t c = blockIdx.x * 8u + (uint32_t)warp;
-  if (c >= s.ncells) return;
+__device__ __forceinline__ void part_scan_warp_cell(const StepDev& s, uint32_t c) {
+  const int lane = threadIdx.x & 31;
   const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
   uint32_t run = 0;
   for (uint32_t j0 = tb; j0 < te; j0 += 32) {
@@ -923,15 +976,18 @@ __global__ void __launch_bounds__(256) k_part_scan_warp(StepDev s) {
   if (lane == 0) s.lcount[c] = run;
 }
 
+__global__ void __launch_bounds__(256) k_part_scan_warp(StepDev s) {
+  const uint32_t nc = ncells_of(s);
+  for (uint32_t c = blockIdx.x * 8u + (threadIdx.x >> 5); c < nc; c += gridDim.x * 8u) part_scan_warp_cell(s, c);
+}
+
 // One warp per cell (widest spread): the key coordinate of each big child,
 // and of each child queued for the subtree kernel (its first level), from its
 // min and max key per coordinate (reduced by the scatter): the
 // largest range (double)max - (double)min, 0 for equal keys, lowest
 // coordinate on ties.
-__global__ void __launch_bounds__(256) k_child_dims(const TreeDev* trees, StepDev s) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t c = blockIdx.x * 8u + (uint32_t)warp;
-  if (c >= s.ncells) return;
+__device__ __forceinline__ void child_dims_cell(const TreeDev* trees, const StepDev& s, uint32_t c) {
+  const int lane = threadIdx.x & 31;
   const Cell cell = s.cells[c];
   const TreeDev& t = trees[cell.tree];
   if (t.key_rule != KEY_WIDEST) return;
@@ -967,15 +1023,18 @@ __global__ void __launch_bounds__(256) k_child_dims(const TreeDev* trees, StepDe
   }
 }
 
+__global__ void __launch_bounds__(256, 1) k_child_dims(const TreeDev* trees, StepDev s) {
+  const uint32_t nc = ncells_of(s);
+  for (uint32_t c = blockIdx.x * 8u + (threadIdx.x >> 5); c < nc; c += gridDim.x * 8u) child_dims_cell(trees, s, c);
+}
+
 // ------------------------------------------------------------- children
 
 // One thread per cell, after the children's sizes are known and before the
 // move: terminal children are recorded, small ones queued for the subtree
 // kernel, big ones get a slot of the next step and a row of its subset
 // offsets (which the scatter fills).
-__global__ void k_classify(const TreeDev* trees, StepDev s) {
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= s.ncells) return;
+__device__ __forceinline__ void classify_cell(const TreeDev* trees, const StepDev& s, uint32_t c) {
   const Cell cell = s.cells[c];
   const TreeDev& t = trees[cell.tree];
   const uint32_t L = s.lcount[c], R = cell.count - L;
@@ -1026,6 +1085,12 @@ __global__ void k_classify(const TreeDev* trees, StepDev s) {
   if (live_delta) atomicAdd(t.live, live_delta);
 }
 
+__global__ void k_classify(const TreeDev* trees, StepDev s) {
+  const uint32_t nc = ncells_of(s);
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+    classify_cell(trees, s, c);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ launcher
@@ -1039,10 +1104,18 @@ cudaError_t prepare_step_kernels() {
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
                      uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d, int uniform_d,
                      const SelectTuning& tune, uint64_t points, uint32_t sms, cudaStream_t st) {
+  // s.ncells: the step's cells, or (s.ncells_dev set: a step inside a graph)
+  // their capacity; per-cell kernels stride over the cells, so their grids
+  // cover the cells exactly here and are capped there
   const uint32_t nc = s.ncells;
   if (nc == 0) return;
+  const bool dev = s.ncells_dev != nullptr;
+  auto cells_grid = [&](uint32_t per_block, uint32_t cap) {
+    const uint32_t g = (nc + per_block - 1) / per_block;
+    return std::max<uint32_t>(1, dev ? std::min(g, cap) : g);
+  };
   { TraceScope ts(K_PREP, st); k_prep<<<1, 1024, 0, st>>>(trees, s); }
-  { TraceScope ts(K_TILES, st); k_tiles<<<nc, 256, 0, st>>>(trees, s); }
+  { TraceScope ts(K_TILES, st); k_tiles<<<cells_grid(1, sms * 8u), 256, 0, st>>>(trees, s); }
   if (has_roots) {
     { TraceScope ts(K_PS_COUNT, st, points); k_ps_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
     { TraceScope ts(K_PS_OFFSETS, st); k_ps_offsets<<<nc, 1024, 0, st>>>(trees, s); }
@@ -1052,7 +1125,7 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
     { TraceScope ts(K_MINMAX, st, points); k_minmax<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
     { TraceScope ts(K_PICK_DIM, st); k_pick_dim<<<nc, 1024, 0, st>>>(trees, s); }
   }
-  { TraceScope ts(K_SEGS, st); k_segs<<<nc, 256, 0, st>>>(trees, s); }
+  { TraceScope ts(K_SEGS, st); k_segs<<<cells_grid(1, sms * 8u), 256, 0, st>>>(trees, s); }
   {
     TraceScope ts(K_SELECT_TINY, st, points);
     k_select_tiny<<<std::max<uint32_t>(1, std::min<uint32_t>((nseg + 255) / 256, sms * 16u)), 256, 0, st>>>(trees, s);
@@ -1077,26 +1150,51 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
     }
   }
   // a CTA per cell while cells are few (large subset counts, deep scans),
-  // a warp per cell once they are many
-  const bool many = nc >= kManyCells;
+  // a warp per cell once they are many (and in a graph, where the count is
+  // not known when the launch is recorded)
+  const bool many = dev || nc >= kManyCells;
   {
     TraceScope ts(K_COMBINE, st);
     if (many)
-      k_combine_warp<<<(nc + 7) / 8, 256, 0, st>>>(trees, s);
+      k_combine_warp<<<cells_grid(8, sms * 8u), 256, 0, st>>>(trees, s);
     else
       k_combine<<<nc, 256, 0, st>>>(trees, s);
   }
-  { TraceScope ts(K_PART_COUNT, st, points); k_part_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
+  {
+    TraceScope ts(K_PART_COUNT, st, points);
+    k_part_count<<<dev ? std::min(max_tiles, sms * 8u) : max_tiles, kTileThreads, 0, st>>>(trees, s);
+  }
   {
     TraceScope ts(K_PART_SCAN, st);
     if (many)
-      k_part_scan_warp<<<(nc + 7) / 8, 256, 0, st>>>(s);
+      k_part_scan_warp<<<cells_grid(8, sms * 8u), 256, 0, st>>>(s);
     else
       k_part_scan<<<nc, 1024, 0, st>>>(s);
   }
-  { TraceScope ts(K_CLASSIFY, st); k_classify<<<(nc + 255) / 256, 256, 0, st>>>(trees, s); }
+  { TraceScope ts(K_CLASSIFY, st); k_classify<<<cells_grid(256, sms * 4u), 256, 0, st>>>(trees, s); }
   launch_scatter(trees, s, max_tiles, 2 * sms, points, uniform_d, st);
-  if (any_widest) { TraceScope ts(K_CHILD_DIMS, st); k_child_dims<<<(nc + 7) / 8, 256, 0, st>>>(trees, s); }
+  if (any_widest) {
+    TraceScope ts(K_CHILD_DIMS, st);
+    k_child_dims<<<cells_grid(8, sms * 8u), 256, 0, st>>>(trees, s);
+  }
+}
+
+namespace {
+
+// Last node of a graph's loop body: count the iteration and keep looping
+// while the next step has cells (at most `limit` iterations).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const uint32_t* ncells_next, uint32_t* iters,
+                            uint32_t limit) {
+  const uint32_t it = *iters + 1u;
+  *iters = it;
+  cudaGraphSetConditional(h, (*ncells_next > 0u && it < limit) ? 1u : 0u);
+}
+
+}  // namespace
+
+void launch_loop_cond(cudaGraphConditionalHandle h, const uint32_t* ncells_next, uint32_t* iters, uint32_t limit,
+                      cudaStream_t st) {
+  k_loop_cond<<<1, 1, 0, st>>>(h, ncells_next, iters, limit);
 }
 
 }  // namespace kdt

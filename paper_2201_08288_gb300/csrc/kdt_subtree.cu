@@ -130,9 +130,10 @@ __device__ __forceinline__ void scan_flags(const uint16_t* f, uint16_t* pre, uin
 }
 
 __global__ void __launch_bounds__(T, kSubtreeCtasPerSm)
-k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head, LCell* slices,
-          uint32_t slice_cells) {
+k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t* count_dev, uint32_t* head,
+          LCell* slices, uint32_t slice_cells) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
+  if (count_dev) count = min(*count_dev, count);  // a graph-driven step: the queue's length, capped
   __shared__ uint32_t tmp[33];
   __shared__ uint32_t s_item, s_ncur, s_nbig, s_where, s_fail;
   __shared__ __align__(8) uint64_t s_bar;
@@ -738,12 +739,13 @@ cudaError_t prepare_subtree_kernel() {
                               (int)kSubtreeSmemBytes);
 }
 
-void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, uint32_t* head, LCell* slices,
-                    uint32_t slice_cells, uint32_t grid, uint64_t points, cudaStream_t st) {
+void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t* count_dev,
+                    uint32_t* head, LCell* slices, uint32_t slice_cells, uint32_t grid, uint64_t points,
+                    cudaStream_t st) {
   if (count == 0) return;
   cudaMemsetAsync(head, 0, sizeof(uint32_t), st);
   TraceScope ts(K_SUBTREE, st, points);
-  k_subtree<<<grid, T, kSubtreeSmemBytes, st>>>(trees, list, count, head, slices, slice_cells);
+  k_subtree<<<grid, T, kSubtreeSmemBytes, st>>>(trees, list, count, count_dev, head, slices, slice_cells);
 }
 
 void launch_finalize_many(const TreeDev* trees, const uint32_t* slots, uint32_t nslots, uint32_t max_records,

@@ -41,10 +41,19 @@ Tracer& tracer() {
 
 }  // namespace
 
+// A launch recorded into a graph (stream capture) is counted but not timed:
+// its events would be replayed by every launch of the graph.
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+void trace_add_launches(uint64_t n) { tracer().launches.fetch_add(n, std::memory_order_relaxed); }
+
 TraceScope::TraceScope(KernelId id, cudaStream_t st, uint64_t units) : id_(id), st_(st), units_(units) {
   Tracer& t = tracer();
   t.launches.fetch_add(1, std::memory_order_relaxed);
-  if (t.on.load(std::memory_order_relaxed)) {
+  if (t.on.load(std::memory_order_relaxed) && !capturing(st_)) {
     if (cudaEventCreate(&start_) == cudaSuccess) {
       cudaEventRecord(start_, st_);
     } else {
@@ -61,7 +70,7 @@ TraceScope::~TraceScope() {
     const char* v = std::getenv("KDT_SYNC_CHECK");
     return v && *v && *v != '0';
   }();
-  if (sync_check) {
+  if (sync_check && !capturing(st_)) {
     const cudaError_t e = cudaStreamSynchronize(st_);
     if (e != cudaSuccess) std::fprintf(stderr, "kdt: %s: %s\n", kNames[id_], cudaGetErrorString(e));
   }

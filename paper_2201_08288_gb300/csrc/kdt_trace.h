@@ -17,6 +17,11 @@ enum KernelId {
   K_LEAF_SCATTER, K_LEAF_COPY, K_NUM
 };
 
+// Launches replayed by a graph beyond the ones counted while it was captured.
+void trace_add_launches(uint64_t n);
+// True while `st` is being captured into a graph.
+bool capturing(cudaStream_t st);
+
 class TraceScope {
  public:
   // units: work items the launch processes (points), for bandwidth figures
