@@ -36,9 +36,9 @@ namespace {
 
 constexpr int kItems = kTile / kTileThreads;
 constexpr int kWarps = kTileThreads / 32;
-constexpr int kPsGroup = 4;                       // tiles per block of the root presort
+constexpr int kPsGroup = 2;                       // tiles per block of the root presort
 constexpr int kPsPoints = kPsGroup * kTile;
-constexpr int kPsThreads = 1024;
+constexpr int kPsThreads = 512;
 constexpr int kPsItems = kPsPoints / kPsThreads;
 constexpr size_t kPsSmemBytes = (size_t)kPsPoints * 6;  // one word and one u16 subset per point
 
@@ -891,10 +891,12 @@ __global__ void __launch_bounds__(256, 1) k_combine_warp(const TreeDev* trees, S
 
 // ------------------------------------------------------------ partition
 
-// Per tile: number of points with key <= split. The tile's key range is
-// read 16 bytes at a time (its unaligned head and tail by single words).
-__device__ __forceinline__ void part_count_tile(const TreeDev* trees, const StepDev& s, uint32_t tile, uint2 tl,
-                                                uint32_t* red) {
+// Per tile: number of points with key <= split. One warp per tile: the
+// tile's key range is read 16 bytes at a time with all of a lane's loads in
+// flight together (its unaligned head and tail by single words).
+__device__ __forceinline__ void part_count_tile(const TreeDev* trees, const StepDev& s, uint32_t tile, uint2 tl) {
+  constexpr int kV = kTile / 4 / 32;  // 16-byte vectors per lane of a full tile
+  const int lane = threadIdx.x & 31;
   const Cell cell = s.cells[tl.x];
   const TreeDev& t = trees[cell.tree];
   const float* X = src_cols(t, cell.level) + (int64_t)s.kdim[tl.x] * t.n + cell.begin + tl.y;
@@ -903,38 +905,28 @@ __device__ __forceinline__ void part_count_tile(const TreeDev* trees, const Step
   const uint32_t head = min(cnt_pts, (4u - (uint32_t)(((uintptr_t)X >> 2) & 3u)) & 3u);
   const uint32_t nv = (cnt_pts - head) >> 2, tail0 = head + nv * 4u;
   const float4* xv = (const float4*)(X + head);  // 16-byte aligned
-  constexpr int kV = kItems / 4;                 // vectors per thread of a full tile
   float4 v[kV];
 #pragma unroll
   for (int q = 0; q < kV; ++q) {
-    const uint32_t i = threadIdx.x + q * kTileThreads;
+    const uint32_t i = (uint32_t)(lane + q * 32);
     v[q] = i < nv ? __ldg(xv + i) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   uint32_t cnt = 0;
 #pragma unroll
   for (int q = 0; q < kV; ++q)
-    if (threadIdx.x + q * kTileThreads < nv)
+    if ((uint32_t)(lane + q * 32) < nv)
       cnt += (ord_key(v[q].x) <= m) + (ord_key(v[q].y) <= m) + (ord_key(v[q].z) <= m) + (ord_key(v[q].w) <= m);
-  if (threadIdx.x < head) cnt += ord_key(__ldg(X + threadIdx.x)) <= m;
-  if (threadIdx.x < cnt_pts - tail0) cnt += ord_key(__ldg(X + tail0 + threadIdx.x)) <= m;
+  if ((uint32_t)lane < head) cnt += ord_key(__ldg(X + lane)) <= m;
+  if ((uint32_t)lane < cnt_pts - tail0) cnt += ord_key(__ldg(X + tail0 + lane)) <= m;
   cnt = __reduce_add_sync(0xffffffffu, cnt);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t tot = 0;
-    for (int w = 0; w < kWarps; ++w) tot += red[w];
-    s.tile_left[tile] = tot;
-  }
+  if (lane == 0) s.tile_left[tile] = cnt;
 }
 
-// CTAs stride over the tiles (one per CTA when the grid covers them).
-__global__ void __launch_bounds__(kTileThreads) k_part_count(const TreeDev* trees, StepDev s) {
-  __shared__ uint32_t red[kWarps];
+// Warps stride over the tiles.
+__global__ void __launch_bounds__(256) k_part_count(const TreeDev* trees, StepDev s) {
   const uint32_t ntiles = *s.ntiles_total;
-  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    part_count_tile(trees, s, tile, s.tiles[tile], red);
-    __syncthreads();  // red is reused by the next tile
-  }
+  for (uint32_t tile = blockIdx.x * 8u + (threadIdx.x >> 5); tile < ntiles; tile += gridDim.x * 8u)
+    part_count_tile(trees, s, tile, s.tiles[tile]);
 }
 
 // One CTA per cell: exclusive scan of its tiles' left counts.
@@ -1162,7 +1154,7 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
   }
   {
     TraceScope ts(K_PART_COUNT, st, points);
-    k_part_count<<<dev ? std::min(max_tiles, sms * 8u) : max_tiles, kTileThreads, 0, st>>>(trees, s);
+    k_part_count<<<std::max<uint32_t>(1, std::min((max_tiles + 7) / 8, sms * 16u)), 256, 0, st>>>(trees, s);
   }
   {
     TraceScope ts(K_PART_SCAN, st);
