@@ -173,8 +173,12 @@ __global__ void __launch_bounds__(kLsThreads) k_leaf_sort(const TreeDev* trees, 
   const TreeDev& t = trees[slots[si]];
   const uint32_t nrec = min(*t.term_count, t.term_cap);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t rec = blockIdx.x * kLsWarps + warp; rec < nrec; rec += gridDim.x * kLsWarps) {
-    const TermRec tr = t.terms[rec];
+  const uint32_t wstride = gridDim.x * kLsWarps;
+  uint32_t rec = blockIdx.x * kLsWarps + warp;
+  TermRec trn = rec < nrec ? t.terms[rec] : TermRec{};
+  for (; rec < nrec; rec += wstride) {
+    const TermRec tr = trn;  // the next record is read before this cell is sorted
+    if (rec + wstride < nrec) trn = t.terms[rec + wstride];
     if (tr.count <= 1u) continue;
     if (tr.count <= (uint32_t)kLeafWarpMax) {
       warp_sort_any(t.out_perm + tr.begin, tr.count);
@@ -183,11 +187,24 @@ __global__ void __launch_bounds__(kLsThreads) k_leaf_sort(const TreeDev* trees, 
       if (k < t.huge_cap) t.huge[k] = rec; else set_status(t, ST_CAPACITY);
     }
   }
+  // the middle cells: the CTA reads kLsThreads records at once and sorts the
+  // ones of its chunk that need a CTA, one after another
+  __shared__ uint32_t mids[kLsThreads];
+  __shared__ uint32_t nmid;
   const int digits = index_digits((uint64_t)t.n);
-  for (uint32_t rec = blockIdx.x; rec < nrec; rec += gridDim.x) {
-    const TermRec tr = t.terms[rec];
-    if (tr.count <= (uint32_t)kLeafWarpMax || tr.count > (uint32_t)kLeafBlockMax) continue;
-    block_sort_slice(t.out_perm + tr.begin, tr.count, digits, S);
+  for (uint32_t base = blockIdx.x * kLsThreads; base < nrec; base += gridDim.x * kLsThreads) {
+    if (threadIdx.x == 0) nmid = 0;
+    __syncthreads();
+    const uint32_t rec = base + threadIdx.x;
+    const uint32_t cnt = rec < nrec ? t.terms[rec].count : 0u;
+    if (cnt > (uint32_t)kLeafWarpMax && cnt <= (uint32_t)kLeafBlockMax) mids[atomicAdd(&nmid, 1u)] = rec;
+    __syncthreads();
+    const uint32_t nm = nmid;
+    for (uint32_t j = 0; j < nm; ++j) {
+      const TermRec tr = t.terms[mids[j]];
+      block_sort_slice(t.out_perm + tr.begin, tr.count, digits, S);
+    }
+    __syncthreads();  // mids and nmid are reused by the next chunk
   }
 }
 
