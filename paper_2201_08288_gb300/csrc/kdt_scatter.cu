@@ -497,9 +497,11 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           }
         }
       }
-      // ---- release the buffer (reads of it precede the next bulk writes)
+      // ---- release the buffer: each warp's reads of it precede the next bulk
+      // writes; the "empty" barrier counts the consumer warps (the next
+      // sub-tile's first barrier orders the reuse of wcnt and sedge)
       fence_proxy_async_smem();
-      named_sync(kConsumerBar, kCT);
+      __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
     }
   }
