@@ -118,29 +118,48 @@ __device__ __forceinline__ bool presort_tile(const TreeDev* trees, const StepDev
   return cell->level == 0 && trees[cell->tree].presorted;
 }
 
-// Per tile of a presorted root with explicit subset ids: points per subset.
+// Points per subset of every presorted root with explicit subset ids. Each
+// CTA counts a contiguous range of tiles into a shared histogram and adds it
+// to the root's totals (root_cur) when the range moves to another tree and at
+// its end.
 __global__ void __launch_bounds__(kTileThreads) k_ps_count(const TreeDev* trees, StepDev s) {
-  uint2 tl;
-  Cell cell;
-  if (!presort_tile(trees, s, blockIdx.x, &tl, &cell)) return;
-  const TreeDev& t = trees[cell.tree];
-  if (t.subset_mode != SUB_EXPLICIT) return;
   __shared__ uint32_t hist[kMaxSubsets];
-  for (int j = threadIdx.x; j < t.r; j += blockDim.x) hist[j] = 0;
-  __syncthreads();
-  const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
-  uint32_t sub[kItems];
+  const uint32_t ntiles = *s.ntiles_total;
+  const uint32_t t_begin = (uint32_t)(((uint64_t)blockIdx.x * ntiles) / gridDim.x);
+  const uint32_t t_end = (uint32_t)(((uint64_t)(blockIdx.x + 1) * ntiles) / gridDim.x);
+  int32_t cur = -1;  // tree whose counts hist holds
+  auto flush = [&]() {
+    __syncthreads();
+    if (cur >= 0) {
+      const TreeDev& t = trees[cur];
+      for (int j = threadIdx.x; j < t.r; j += blockDim.x)
+        if (hist[j]) atomicAdd(&t.root_cur[j], hist[j]);
+    }
+    __syncthreads();
+  };
+  for (uint32_t tile = t_begin; tile < t_end; ++tile) {
+    const uint2 tl = s.tiles[tile];
+    const Cell cell = s.cells[tl.x];
+    const TreeDev& t = trees[cell.tree];
+    if (cell.level != 0 || !t.presorted || t.subset_mode != SUB_EXPLICIT) continue;
+    if (cell.tree != cur) {
+      flush();
+      for (int j = threadIdx.x; j < t.r; j += blockDim.x) hist[j] = 0;
+      cur = cell.tree;
+      __syncthreads();
+    }
+    const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
+    uint32_t sub[kItems];
 #pragma unroll
-  for (int q = 0; q < kItems; ++q) {
-    const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
-    sub[q] = i < end ? subset_of(t, t.sid_in, 0u, (int64_t)i) : 0xffffffffu;
+    for (int q = 0; q < kItems; ++q) {
+      const uint32_t i = tl.y + threadIdx.x + q * kTileThreads;
+      sub[q] = i < end ? subset_of(t, t.sid_in, 0u, (int64_t)i) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int q = 0; q < kItems; ++q)
+      if (sub[q] != 0xffffffffu) atomic_add_shared(&hist[sub[q]], 1u);
   }
-#pragma unroll
-  for (int q = 0; q < kItems; ++q)
-    if (sub[q] != 0xffffffffu) atomic_add_shared(&hist[sub[q]], 1u);
-  __syncthreads();
-  for (int j = threadIdx.x; j < t.r; j += blockDim.x)
-    if (hist[j]) atomicAdd(&t.root_cur[j], hist[j]);
+  flush();
 }
 
 // One CTA per root cell: its subset offsets (r + 1 entries). Explicit ids:
@@ -1109,7 +1128,10 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
   { TraceScope ts(K_PREP, st); k_prep<<<1, 1024, 0, st>>>(trees, s); }
   { TraceScope ts(K_TILES, st); k_tiles<<<cells_grid(1, sms * 8u), 256, 0, st>>>(trees, s); }
   if (has_roots) {
-    { TraceScope ts(K_PS_COUNT, st, points); k_ps_count<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
+    {
+      TraceScope ts(K_PS_COUNT, st, points);
+      k_ps_count<<<std::max<uint32_t>(1, std::min(max_tiles, sms * 4u)), kTileThreads, 0, st>>>(trees, s);
+    }
     { TraceScope ts(K_PS_OFFSETS, st); k_ps_offsets<<<nc, 1024, 0, st>>>(trees, s); }
     { TraceScope ts(K_PS_MOVE, st, points); k_ps_move<<<max_tiles, kPsThreads, kPsSmemBytes, st>>>(trees, s); }
   }
