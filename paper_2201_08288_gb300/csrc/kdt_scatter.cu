@@ -63,7 +63,9 @@ struct SubMeta {
   uint32_t prev_sub;   // subset of the point before the sub-tile (~0u at the cell's start)
   uint32_t r, subset_mode, sid_bytes, sid_ph, tn;
   int32_t d;
-  uint8_t term_left, term_right, want_mm, want_off, level0, pad0, pad1, pad2;
+  uint8_t term_left, term_right, want_mm, want_off, level0;
+  uint8_t run_more;  // this CTA's next tile is of the same cell (its min / max run goes on)
+  uint8_t pad1, pad2;
   uint32_t ph[kMaxDims + 1];  // alignment phase of each staged word column
 };
 
@@ -115,6 +117,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         tl_next = s.tiles[tile + 1];
         c_next = s.cells[tl_next.x];
       }
+      const bool run_more = tile + 1 < t_end && tl_next.x == tl.x;
       const TreeDev& tg = trees[c.tree];
       const int d = kD > 0 ? kD : tg.d, ncols = d + 1;
       const bool expl = tg.subset_mode == SUB_EXPLICIT;
@@ -187,6 +190,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           m.want_mm = tg.key_rule == KEY_WIDEST && !(term_left && term_right);
           m.want_off = cr0.x != kNoRow || cr1.x != kNoRow;
           m.level0 = c.level == 0;
+          m.run_more = run_more;
         }
         uint32_t total = expl ? (sa1 - sa0) * (uint32_t)es : 0u;
         for (int c0 = 0; c0 < ncols; c0 += 32) {
@@ -466,11 +470,10 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         if (saw_nan) atomicCAS(m.status, ST_OK, ST_NAN_INPUT);
         saw_nan = false;
         if (want_mm) {
-          // keep reducing while this CTA's next tile is of the same cell;
-          // else add the run's min / max to the cell's with atomics
-          const uint32_t nt = tile + 1;
-          const bool same = nt < t_end && s.tiles[nt].x == m.cell_idx;
-          if (!same) {
+          // keep reducing while this CTA's next tile is of the same cell (the
+          // producer, which reads the tile list ahead, says so); else add the
+          // run's min / max to the cell's with atomics
+          if (!m.run_more) {
             if (kAcc) {
 #pragma unroll
               for (int l = 0; l < kAD; ++l)
