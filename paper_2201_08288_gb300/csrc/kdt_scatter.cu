@@ -176,9 +176,6 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           m.tile_start = tl.y;
           m.row[0] = cr0.x == kNoRow ? kNoRow : cr0.y;
           m.row[1] = cr1.x == kNoRow ? kNoRow : cr1.y;
-          m.prev_sub = (sub > 0u && (cr0.x != kNoRow || cr1.x != kNoRow))
-                           ? subset_at(tg, c.level, (int64_t)g0 - 1)
-                           : 0xffffffffu;
           m.r = (uint32_t)tg.r;
           m.subset_mode = (uint32_t)tg.subset_mode;
           m.sid_bytes = (uint32_t)es;
@@ -239,6 +236,11 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         }
         if (!P)
           for (uint32_t i = lane; i < mcnt; i += 32) A[(size_t)d * stride + i] = g0 + i;
+        // the subset of the point before the sub-tile: a global load, read once
+        // the copies are on their way
+        if (lane == 0)
+          m.prev_sub = (sub > 0u && (cr0.x != kNoRow || cr1.x != kNoRow)) ? subset_at(tg, c.level, (int64_t)g0 - 1)
+                                                                          : 0xffffffffu;
         cp_async_mbar_arrive(&full[b]);  // this lane's edge copies count toward the phase
         __syncwarp();
         if (lane == 0) mbar_arrive(&full[b]);
