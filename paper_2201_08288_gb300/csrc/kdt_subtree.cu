@@ -317,7 +317,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
             for (int c0 = 0; c0 < d; c0 += 8) {
               const int nc = min(8, d - c0);
               uint32_t base[8], lo[8], hi[8];
-  #pragma unroll
+#pragma unroll
               for (int q = 0; q < 8; ++q) {
                 base[q] = q < nc ? s_colbase[c0 + q] : 0u;
                 lo[q] = 0xffffffffu;
@@ -325,7 +325,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
               }
               for (uint32_t i = i0 + lane; i < i1; i += 32) {
                 const uint32_t o = ordA[i];
-  #pragma unroll
+#pragma unroll
                 for (int q = 0; q < 8; ++q)
                   if (q < nc) {
                     const uint32_t kk = S.cols[base[q] + o];
@@ -333,7 +333,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
                     hi[q] = max(hi[q], kk);
                   }
               }
-  #pragma unroll
+#pragma unroll
               for (int q = 0; q < 8; ++q)
                 if (q < nc) {
                   const uint32_t l = __reduce_min_sync(0xffffffffu, lo[q]);
@@ -611,7 +611,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
             const int stall = (R == 0) ? p.stall + 1 : 0;
             const uint32_t cbeg[2] = {p.begin, p.begin + L};
             const uint32_t cn[2] = {L, R};
-  #pragma unroll
+#pragma unroll
             for (int side = 0; side < 2; ++side) {
               const uint32_t heap = 2u * p.heap + 1u + (uint32_t)side;
               if (is_terminal(t, cn[side], nlevel, stall)) {
