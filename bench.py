@@ -42,6 +42,8 @@ def workload(name: str, rank: int):
         spec = W.config1()
     elif name == "c3s":  # profiling case: config 3's recipe at n=2^22 (larger than L2, small for ncu)
         spec = W.config3(n=1 << 22, depth=15)
+    elif name == "w6":  # Sec. 5's simulation shape: trivariate normal, correlation 0.5, n=2^27, depth 10
+        spec = W.paper_mvn(1 << 27, 0.5, 10)
     else:
         raise SystemExit(f"unknown workload {name}")
     spec.seed += 1000 * rank
@@ -158,7 +160,7 @@ def cpu_baseline(name: str, target_s: float = 12.0) -> dict:
     while True:
         depth_s = max(1, full_depth - int(round(np.log2(full_n / n_s))))
         s = W.TreeSpec(spec.name, n_s, spec.d, spec.dist, spec.seed, spec.r, spec.subset_mode, spec.key_rule,
-                       depth=depth_s, sid_seed=spec.sid_seed)
+                       depth=depth_s, sid_seed=spec.sid_seed, rho=spec.rho)
         pts, sid = s.points(), s.sids()
         t0 = time.perf_counter()
         t = oracle.build_tree(pts, r=s.r, subset_mode=s.subset_mode, sid=sid, depth=depth_s, key_rule=s.key_rule)
@@ -180,7 +182,7 @@ def run_reference(args) -> None:
     n_s = 1 << 18
     depth_s = max(1, spec.depth - int(round(np.log2(spec.n / n_s))))
     s = W.TreeSpec(spec.name, n_s, spec.d, spec.dist, spec.seed, spec.r, spec.subset_mode, spec.key_rule,
-                   depth=depth_s, sid_seed=spec.sid_seed)
+                   depth=depth_s, sid_seed=spec.sid_seed, rho=spec.rho)
     pts, sid = s.points(), s.sids()
     kw = dict(r=s.r, subset_mode=s.subset_mode, sid=sid, depth=depth_s, key_rule=s.key_rule)
     for _ in range(args.warmup):
@@ -353,7 +355,7 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c3s", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c3s", "w6", "c4", "c5"])
     ap.add_argument("--trees", type=int, default=4096, help="c4: number of trees")
     ap.add_argument("--requests", type=int, default=20000, help="c5: number of requests")
     ap.add_argument("--load", type=float, default=0.7, help="c5: arrival rate / solo capacity")

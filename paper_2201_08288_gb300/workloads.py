@@ -113,6 +113,22 @@ def student_t_snapped_device(n: int, d: int, df: float, snap_frac: float, grid: 
     return out
 
 
+def mvn_common_corr_device(n: int, d: int, rho: float, seed: int, device="cuda"):
+    """Multivariate normal, mean 0, unit variances, common correlation rho, drawn
+    on the device (float64 Cholesky factor applied to float64 normals)."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    cov = np.full((d, d), rho) + (1.0 - rho) * np.eye(d)
+    chol = torch.from_numpy(np.linalg.cholesky(cov)).to(device)
+    out = torch.empty((d, n), device=device, dtype=torch.float32)
+    step = 1 << 24
+    for b in range(0, n, step):
+        e = min(n, b + step)
+        z = torch.randn((d, e - b), generator=g, device=device, dtype=torch.float64)
+        out[:, b:e] = (chol @ z).to(torch.float32)
+    return out
+
+
 def explicit_sids_device(n: int, r: int, seed: int, device="cuda"):
     import torch
     g = torch.Generator(device=device).manual_seed(seed)
@@ -163,6 +179,8 @@ class TreeSpec:
             return gaussian_mixture_device(self.n, self.d, 8, 0.05, self.seed, device)
         if self.dist == "student_t":
             return student_t_snapped_device(self.n, self.d, 3.0, 0.1, 256, self.seed, device)
+        if self.dist == "mvn":
+            return mvn_common_corr_device(self.n, self.d, self.rho, self.seed, device)
         raise ValueError(self.dist)
 
     def sids(self):
