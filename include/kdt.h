@@ -218,7 +218,7 @@ kdt_status kdt_server_destroy(kdt_server *s);
  * trade only speed, and kdt_autotune times them on the caller's own trees.
  */
 typedef struct kdt_tuning {
-  int32_t tiny_max;     /* one thread per segment up to this many keys: 8, 16 or 32    */
+  int32_t tiny_max;     /* one thread per segment up to this many keys: 8 to 64 (x2)   */
   int32_t bitonic_max;  /* a warp's bitonic network up to this many: 64, 128 or 256    */
   int32_t warp_max;     /* a warp's radix select up to this many: 1024, 2048 or 4096   */
   int32_t cta_threads;  /* threads of the CTA radix select: 256 or 512                 */

@@ -29,7 +29,7 @@ constexpr int kMaxSubsets = 4096;     // r <= 4096 on the CUDA path
 constexpr int kMaxLevels = 30;        // depth / max_levels <= 30
 constexpr int kTile = 2048;           // points per tile of the multi-CTA pipeline
 constexpr int kTileThreads = 256;     // threads of the tile kernels
-constexpr int kSelTinyMax = 32;       // segments up to this size: one thread per segment
+constexpr int kSelTinyMax = 64;       // segments up to this size: one thread per segment
 constexpr int kSelSmallMax = 4096;    // largest warp-select segment (kdt_tuning warp_max)
 constexpr int kSelWarpMin = 1024;     // smallest warp_max: sizes the list of CTA-select segments
 constexpr int kSubtreeThreads = 256;  // threads of a CTA of the in-shared-memory subtree kernel

@@ -513,55 +513,76 @@ __global__ void k_segs(const TreeDev* trees, StepDev s) {
 
 // ------------------------------------------------------------ selection
 
-// Lower median of a segment of w <= N keys by one thread: bitonic sorting
-// network over N registers (keys past w padded with the largest key).
-template <int N>
-__device__ __forceinline__ uint32_t thread_lower_median(const uint32_t* keys, uint32_t w) {
-  uint32_t v[N];
+// Batcher's odd-even merge sort of v[0, M) ascending, M a power of two. In
+// the round of merge width 2p and distance k, position x is compared with
+// x + k when x lies in an even block of k positions counted from k mod p and
+// both lie in one block of 2p; every comparator is fixed at compile time.
+template <int M>
+__device__ __forceinline__ void oddeven_sort(uint32_t (&v)[M]) {
 #pragma unroll
-  for (int i = 0; i < N; ++i) v[i] = (uint32_t)i < w ? kload(keys + i) : 0xffffffffu;
+  for (int p = 1; p < M; p <<= 1)
 #pragma unroll
-  for (int size = 2; size <= N; size <<= 1)
+    for (int k = p; k >= 1; k >>= 1)
 #pragma unroll
-    for (int j = size >> 1; j > 0; j >>= 1)
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const int p = i ^ j;
-        if (p > i) {
-          const uint32_t lo = min(v[i], v[p]), hi = max(v[i], v[p]);
-          if ((i & size) == 0) {
-            v[i] = lo;
-            v[p] = hi;
-          } else {
-            v[i] = hi;
-            v[p] = lo;
-          }
+      for (int x = 0; x < M; ++x) {
+        const int j0 = k % p;
+        if (x >= j0 && ((x - j0) / k) % 2 == 0 && x + k < M && x / (2 * p) == (x + k) / (2 * p)) {
+          const uint32_t a = v[x], b = v[x + k];
+          v[x] = min(a, b);
+          v[x + k] = max(a, b);
         }
       }
-  const uint32_t want = (w - 1) / 2;
-  uint32_t med = v[0];
+}
+
+// Lower median (rank (w-1)/2) of a segment of 1 <= w <= 2M keys by one
+// thread. The keys are padded to 2M: M - 1 - (w-1)/2 copies of the smallest
+// key 0, the rest the largest key ~0, so that the median has rank M - 1 among
+// the 2M (padding keys equal to a real key would not change the element at
+// that rank). Both halves are sorted; A ascending followed by B reversed is
+// bitonic, so min(A[i], B[M-1-i]) over i are the M smallest of the 2M, and
+// the largest of them is the element of rank M - 1.
+template <int M>
+__device__ __forceinline__ uint32_t thread_lower_median(const uint32_t* keys, uint32_t w) {
+  const uint32_t zeros_end = w + (uint32_t)(M - 1) - (w - 1u) / 2u;  // [w, zeros_end) hold 0
+  uint32_t a[M], b[M];
 #pragma unroll
-  for (int i = 1; i < N; ++i)
-    if ((uint32_t)i == want) med = v[i];
+  for (int i = 0; i < M; ++i) {
+    const uint32_t e = (uint32_t)i, f = (uint32_t)(i + M);
+    a[i] = e < w ? kload(keys + e) : (e < zeros_end ? 0u : 0xffffffffu);
+    b[i] = f < w ? kload(keys + f) : (f < zeros_end ? 0u : 0xffffffffu);
+  }
+  oddeven_sort<M>(a);
+  oddeven_sort<M>(b);
+  uint32_t med = 0u;
+#pragma unroll
+  for (int i = 0; i < M; ++i) med = max(med, min(a[i], b[M - 1 - i]));
   return med;
 }
 
-// One thread per segment of at most tiny_max <= kSelTinyMax points (threads stride over
-// the segments of the step).
+// One thread per segment of at most tiny_max <= kSelTinyMax points (the
+// threads stride over the segments of the step). The network's size is
+// chosen per warp, by the warp's largest segment, so a warp never runs two.
 __global__ void __launch_bounds__(256) k_select_tiny(const TreeDev* trees, StepDev s) {
   const uint32_t nseg = s.seg_base[ncells_of(s)];
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nseg; g += gridDim.x * blockDim.x) {
-    const uint32_t w = s.seg_w[g];
-    if (w == 0 || w > s.tiny_max) continue;
-    const uint32_t* keys = s.seg_key[g];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t g0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); g0 < nseg; g0 += stride) {
+    const uint32_t g = g0 + lane;
+    uint32_t w = g < nseg ? s.seg_w[g] : 0u;
+    if (w > s.tiny_max) w = 0u;
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, w);
+    if (wmax == 0u) continue;
+    const uint32_t* keys = w ? s.seg_key[g] : nullptr;
     uint32_t med;
-    if (w <= 8)
+    if (wmax <= 8u)
+      med = thread_lower_median<4>(keys, w);
+    else if (wmax <= 16u)
       med = thread_lower_median<8>(keys, w);
-    else if (w <= 16)
+    else if (wmax <= 32u)
       med = thread_lower_median<16>(keys, w);
     else
       med = thread_lower_median<32>(keys, w);
-    s.seg_med[g] = med;
+    if (w) s.seg_med[g] = med;
   }
 }
 

@@ -14,7 +14,7 @@ namespace kdt {
 namespace {
 
 std::mutex g_mu;
-kdt_tuning g_tuning = {32, 256, 4096, 256, 11, {0, 0, 0}};
+kdt_tuning g_tuning = {64, 256, 4096, 256, 11, {0, 0, 0}};
 
 template <size_t N>
 bool one_of(int32_t v, const int32_t (&choices)[N]) {
@@ -23,7 +23,7 @@ bool one_of(int32_t v, const int32_t (&choices)[N]) {
   return false;
 }
 
-const int32_t kTiny[] = {8, 16, 32};
+const int32_t kTiny[] = {8, 16, 32, 64};
 const int32_t kBitonic[] = {64, 128, 256};
 const int32_t kWarp[] = {1024, 2048, 4096};
 const int32_t kThreads[] = {256, 512};
@@ -48,7 +48,7 @@ SelectTuning current_tuning() {
 extern "C" {
 
 void kdt_tuning_default(kdt_tuning* t) {
-  if (t) *t = kdt_tuning{32, 256, 4096, 256, 11, {0, 0, 0}};
+  if (t) *t = kdt_tuning{64, 256, 4096, 256, 11, {0, 0, 0}};
 }
 
 kdt_status kdt_set_tuning(const kdt_tuning* t) {
@@ -127,7 +127,7 @@ kdt_status kdt_autotune(const kdt_tree_desc* trees, int32_t num_trees, void* wor
     const int32_t* choices;
     int n;
   };
-  const Field fields[] = {{&kdt_tuning::tiny_max, kdt::kTiny, 3},
+  const Field fields[] = {{&kdt_tuning::tiny_max, kdt::kTiny, 4},
                           {&kdt_tuning::bitonic_max, kdt::kBitonic, 3},
                           {&kdt_tuning::warp_max, kdt::kWarp, 3},
                           {&kdt_tuning::cta_threads, kdt::kThreads, 2},

@@ -88,7 +88,7 @@ class kdt_tuning(ctypes.Structure):
 
 TUNING_FIELDS = ("tiny_max", "bitonic_max", "warp_max", "cta_threads", "digit_bits")
 # the choices kdt_set_tuning accepts, per field
-TUNING_CHOICES = {"tiny_max": (8, 16, 32), "bitonic_max": (64, 128, 256), "warp_max": (1024, 2048, 4096),
+TUNING_CHOICES = {"tiny_max": (8, 16, 32, 64), "bitonic_max": (64, 128, 256), "warp_max": (1024, 2048, 4096),
                   "cta_threads": (256, 512), "digit_bits": (8, 11)}
 
 

@@ -85,7 +85,7 @@ def test_tuning_set_get_and_validation_need_no_gpu(lib):
     every field, and rejection of anything else (the tuning in force kept)."""
     from paper_2201_08288_gb300 import kdt
     d = kdt.tuning_default()
-    assert d == {"tiny_max": 32, "bitonic_max": 256, "warp_max": 4096, "cta_threads": 256, "digit_bits": 11}
+    assert d == {"tiny_max": 64, "bitonic_max": 256, "warp_max": 4096, "cta_threads": 256, "digit_bits": 11}
     kdt.set_tuning(None)
     assert kdt.get_tuning() == d
     try:
@@ -96,7 +96,7 @@ def test_tuning_set_get_and_validation_need_no_gpu(lib):
                 kdt.set_tuning(t)
                 assert kdt.get_tuning() == t
         kept = kdt.get_tuning()
-        for f, bad in [("tiny_max", 0), ("tiny_max", 64), ("bitonic_max", 32), ("warp_max", 8192),
+        for f, bad in [("tiny_max", 0), ("tiny_max", 128), ("bitonic_max", 32), ("warp_max", 8192),
                        ("cta_threads", 128), ("digit_bits", 4)]:
             t = dict(d)
             t[f] = bad
