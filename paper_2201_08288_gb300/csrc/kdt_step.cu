@@ -586,21 +586,27 @@ __global__ void __launch_bounds__(256) k_select_tiny(const TreeDev* trees, StepD
   }
 }
 
-// Lower median of w <= 32K keys by one warp: bitonic sorting network over
-// K registers per lane (element e = k * 32 + lane; keys past w padded with
-// the largest key), then the element of rank (w-1)/2.
+// Lower median of 1 <= w <= 32K keys by one warp, element e = k * 32 + lane
+// in register k of a lane. As in thread_lower_median the keys are padded to
+// N = 32K with the smallest and the largest key so that the median has rank
+// N/2 - 1; the bitonic network runs its stages up to size N/2 only, which
+// leaves the first half ascending and the second descending: a bitonic
+// sequence whose half-cleaner min(v[k], v[k + K/2]) holds the N/2 smallest
+// keys, the largest of which (over the warp) is the median.
 template <int K>
 __device__ uint32_t warp_bitonic_median(const uint32_t* keys, uint32_t w) {
+  static_assert(K >= 2 && (K & (K - 1)) == 0, "K: a power of two of at least 2");
   const int lane = threadIdx.x & 31;
+  constexpr int N = 32 * K;
+  const uint32_t zeros_end = w + (uint32_t)(N / 2 - 1) - (w - 1u) / 2u;  // [w, zeros_end) hold 0
   uint32_t v[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const uint32_t e = (uint32_t)(k * 32 + lane);
-    v[k] = e < w ? kload(keys + e) : 0xffffffffu;
+    v[k] = e < w ? kload(keys + e) : (e < zeros_end ? 0u : 0xffffffffu);
   }
-  constexpr int N = 32 * K;
 #pragma unroll
-  for (int size = 2; size <= N; size <<= 1) {
+  for (int size = 2; size <= N / 2; size <<= 1) {
 #pragma unroll
     for (int j = size >> 1; j > 0; j >>= 1) {
 #pragma unroll
@@ -622,12 +628,10 @@ __device__ uint32_t warp_bitonic_median(const uint32_t* keys, uint32_t w) {
       }
     }
   }
-  const uint32_t want = (w - 1) / 2;
-  uint32_t x = v[0];
+  uint32_t m = 0u;
 #pragma unroll
-  for (int k = 1; k < K; ++k)
-    if ((uint32_t)k == want / 32u) x = v[k];
-  return __shfl_sync(0xffffffffu, x, want % 32u);
+  for (int k = 0; k < K / 2; ++k) m = max(m, min(v[k], v[k + K / 2]));
+  return __reduce_max_sync(0xffffffffu, m);
 }
 
 // State of a warp's radix select: the key bits found so far (`prefix`, all
