@@ -477,16 +477,40 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           // run's min / max to the cell's with atomics
           if (!m.run_more) {
             if (kAcc) {
+              // transpose-reduce over the warp: value u = (l * 2 + side) * 2 +
+              // which, maxima negated so that every step is a minimum; after
+              // the steps lane u holds value u reduced over all 32 lanes
+              constexpr int kV = 4 * kAD;
+              constexpr int kVP = kV <= 8 ? 8 : (kV <= 16 ? 16 : 32);
+              float v[kVP];
+#pragma unroll
+              for (int u = 0; u < kVP; ++u) {
+                const int l = u / 4, side = (u / 2) & 1, which = u & 1;
+                v[u] = u >= kV ? inf : (which ? -acc[l % kAD][side][1] : acc[l % kAD][side][0]);
+              }
+#pragma unroll
+              for (int h = kVP / 2; h >= 1; h >>= 1) {
+                const bool upper = (lane & h) != 0;
+#pragma unroll
+                for (int i = 0; i < h; ++i) {
+                  const float keep = upper ? v[i + h] : v[i];
+                  const float send = upper ? v[i] : v[i + h];
+                  v[i] = fminf(keep, __shfl_xor_sync(0xffffffffu, send, h));
+                }
+              }
+#pragma unroll
+              for (int o = kVP; o < 32; o <<= 1) v[0] = fminf(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+              if (lane < kV) {
+                const int l = lane / 4, side = (lane / 2) & 1;
+                if (lane & 1)
+                  atomic_max_shared(&tmm[side][l][1], ord_key(-v[0]));
+                else
+                  atomic_min_shared(&tmm[side][l][0], ord_key(v[0]));
+              }
 #pragma unroll
               for (int l = 0; l < kAD; ++l)
 #pragma unroll
                 for (int side = 0; side < 2; ++side) {
-                  const uint32_t lo = __reduce_min_sync(0xffffffffu, ord_key(acc[l][side][0]));
-                  const uint32_t hi = __reduce_max_sync(0xffffffffu, ord_key(acc[l][side][1]));
-                  if (lane == 0) {
-                    atomic_min_shared(&tmm[side][l][0], lo);
-                    atomic_max_shared(&tmm[side][l][1], hi);
-                  }
                   acc[l][side][0] = inf;
                   acc[l][side][1] = -inf;
                 }
