@@ -18,6 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "kdt_oracle.c")
+_SRC_FOURIER = os.path.join(_HERE, "kdt_oracle_fourier.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "libkdt_oracle.so")
 
@@ -55,12 +56,12 @@ def build_library(force: bool = False) -> str:
     """Compile kdt_oracle.c into a shared library (gcc, portable flags)."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_FOURIER),
                                                    os.path.getmtime(os.path.join(_HERE, "kdt_oracle.h")))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra",
-                           "-o", tmp, _SRC, "-lm"])
+                           "-o", tmp, _SRC, _SRC_FOURIER, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -87,6 +88,20 @@ def _load():
                                         ctypes.POINTER(ctypes.c_uint32),
                                         ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int64)]
+        dbl = ctypes.c_double
+        lib.kdto_fourier_c.restype = dbl
+        lib.kdto_fourier_c.argtypes = [ctypes.c_int32, dbl]
+        lib.kdto_fourier_g.restype = dbl
+        lib.kdto_fourier_g.argtypes = [ctypes.c_int32, dbl, dbl]
+        lib.kdto_fourier_moments.restype = ctypes.c_int
+        lib.kdto_fourier_moments.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]
+        lib.kdto_fourier_split.restype = ctypes.c_int
+        lib.kdto_fourier_split.argtypes = [ctypes.c_void_p, ctypes.c_int64, dbl, dbl, ctypes.c_int32,
+                                           ctypes.POINTER(dbl)]
+        lib.kdto_fourier_build.restype = ctypes.c_int
+        lib.kdto_fourier_build.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]
         _lib = lib
     return _lib
 
@@ -170,3 +185,73 @@ def split_cell(points: np.ndarray, idx: np.ndarray, level: int, *, r: int = 1,
     if st != 0:
         raise OracleError(st)
     return dim.value, k.value, v.value, left.value
+
+
+# ------------------------------------------------- the paper's estimator
+# (Sec. 3.1 Lemma 1, Sec. 3.2 Eq. (kd:eq:b); readings in kdt_oracle_fourier.c)
+
+FOURIER_MAX_J = 4096
+
+
+def fourier_c(j: int, x: float) -> float:
+    """Basis term c_j(x) of Lemma 1."""
+    return float(_load().kdto_fourier_c(j, x))
+
+
+def fourier_g(j: int, a: float, b: float) -> float:
+    """Coefficient g_j(a, b) of Lemma 1."""
+    return float(_load().kdto_fourier_g(j, a, b))
+
+
+def fourier_moments(x: np.ndarray, J: int) -> np.ndarray:
+    """C_j = sum_i c_j(x_i), j = 0..2J (float64)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(2 * J + 1, np.float64)
+    st = _load().kdto_fourier_moments(x.ctypes.data, x.size, J, out.ctypes.data)
+    if st != 0:
+        raise OracleError(st)
+    return out
+
+
+def fourier_split(x: np.ndarray, a: float, b: float, J: int) -> float:
+    """Root of Eq. (kd:eq:b) on (a, b) for the key values x (float64 bisection)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    m = ctypes.c_double()
+    st = _load().kdto_fourier_split(x.ctypes.data, x.size, a, b, J, ctypes.byref(m))
+    if st != 0:
+        raise OracleError(st)
+    return m.value
+
+
+def fourier_build_tree(points: np.ndarray, *, depth: int, J: int) -> Tree:
+    """Depth-D tree whose splits are the estimator's roots (cyclic keys). points: float32 [d, n] in (0,1)."""
+    points = np.ascontiguousarray(points, dtype=np.float32)
+    d, n = points.shape
+    perm = np.zeros(max(n, 1), np.uint32)
+    vals = np.zeros((1 << depth) - 1, np.float32)
+    dims = np.zeros((1 << depth) - 1, np.int8)
+    offs = np.zeros((1 << depth) + 1, np.int64)
+    st = _load().kdto_fourier_build(points.ctypes.data, n, d, depth, J, perm.ctypes.data, vals.ctypes.data,
+                                    dims.ctypes.data, offs.ctypes.data)
+    if st != 0:
+        raise OracleError(st)
+    return Tree(perm[:n].copy(), vals, dims, offs, depth)
+
+
+def fourier_cell_bounds(split_vals: np.ndarray, heap: int, d: int) -> tuple[float, float]:
+    """Bounds (a, b) of node `heap` on its cyclic key coordinate: the float
+    splits of its ancestors on that coordinate, (0, 1) at the root."""
+    level = int(np.floor(np.log2(heap + 1)))
+    t = level % d
+    a, b, h = 0.0, 1.0, heap
+    while h > 0:
+        par = (h - 1) // 2
+        plevel = int(np.floor(np.log2(par + 1)))
+        if plevel % d == t:
+            v = float(split_vals[par])
+            if h == 2 * par + 1:
+                b = min(b, v)
+            else:
+                a = max(a, v)
+        h = par
+    return a, b

@@ -82,6 +82,31 @@ int kdto_split_cell(const float *points, const kdto_params *p, const int64_t *id
                     int64_t cnt, int32_t level, int32_t *out_dim,
                     uint32_t *out_key, float *out_val, int64_t *out_left);
 
+/* ---- the paper's Fourier-moment estimator (kdt_oracle_fourier.c) ------- */
+
+/* Largest number of harmonics J (terms c_0 .. c_2J) the oracle accepts. */
+#define KDTO_FOURIER_MAX_J 4096
+
+/* Basis term c_j(x) and coefficient g_j(a, b) of Lemma 1 (Sec. 3.1). */
+double kdto_fourier_c(int32_t j, double x);
+double kdto_fourier_g(int32_t j, double a, double b);
+/* out[j] = sum_i c_j(x[i]) for j = 0..2J: the additive statistics of Sec. 3.2. */
+int kdto_fourier_moments(const double *x, int64_t cnt, int32_t J, double *out);
+/*
+ * Root of Eq. (kd:eq:b) on (a, b) for the values x[0..cnt) of the cell's key
+ * coordinate: bisection of F(m) = 1_J(a, m) - 1_J(m, b) (60 halvings, double),
+ * *out_m the midpoint of the last interval. Requires 0 <= a < b <= 1.
+ */
+int kdto_fourier_split(const double *x, int64_t cnt, double a, double b, int32_t J, double *out_m);
+/*
+ * Depth-D tree with cyclic keys whose splits are the estimator's roots
+ * rounded to float; points with coordinate <= split go left (stable).
+ * Every coordinate must lie in (0,1). Outputs as for kdto_build with L = depth.
+ */
+int kdto_fourier_build(const float *points, int64_t n, int32_t d, int32_t depth, int32_t J,
+                       uint32_t *out_perm, float *out_split_vals, int8_t *out_split_dims,
+                       int64_t *out_node_offsets);
+
 #ifdef __cplusplus
 }
 #endif
