@@ -44,13 +44,15 @@ def workload(name: str, rank: int):
         spec = W.config3(n=1 << 22, depth=15)
     elif name == "w6":  # Sec. 5's simulation shape: trivariate normal, correlation 0.5, n=2^27, depth 10
         spec = W.paper_mvn(1 << 27, 0.5, 10)
+    elif name == "w6f":  # the same shape through the normal CDF, split by the paper's estimator (J = 16)
+        spec = W.paper_mvn_fourier(1 << 27, 0.5, 10, 16)
     else:
         raise SystemExit(f"unknown workload {name}")
     spec.seed += 1000 * rank
     if spec.sid_seed is not None:
         spec.sid_seed += 1000 * rank
     kw = dict(r=spec.r, subset_mode=spec.subset_mode, depth=spec.depth, key_rule=spec.key_rule,
-              leaf_size=spec.leaf_size, max_levels=spec.max_levels)
+              leaf_size=spec.leaf_size, max_levels=spec.max_levels, fourier_j=spec.fourier_j)
     return spec, kw
 
 
@@ -62,6 +64,7 @@ def bytes_per_point(kernel: str, d: int, sid_bytes: int, subset_mode: int) -> fl
         "k_ps_move": 2.0 * (4 * d + sid_bytes) + 4,         # columns and ids in and out, perm out
         "k_part_count": 4.0,
         "k_select_small": 4.0,                              # the key column, read in place
+        "k_fourier_moments": 4.0,                           # the key column, read in place
         "k_minmax": 4.0 * d,
     }.get(kernel, 0.0)
 
@@ -148,6 +151,14 @@ def recorded_traffic(kernel: str, workload_name: str):
     return float(rec["dram_bytes_per_point"])
 
 
+def oracle_build(oracle, spec, pts, sid, s, depth_s):
+    """The oracle's build of a sample: the subset-median rule, or the paper's
+    estimator for a workload that splits by it."""
+    if spec.fourier_j > 0:
+        return oracle.fourier_build_tree(pts, depth=depth_s, J=spec.fourier_j)
+    return oracle.build_tree(pts, r=s.r, subset_mode=s.subset_mode, sid=sid, depth=depth_s, key_rule=s.key_rule)
+
+
 def cpu_baseline(name: str, target_s: float = 12.0) -> dict:
     """The oracle as it stands, single-threaded on a host core, on a bounded
     sample of the same workload recipe (fewer points, depth reduced so the
@@ -163,7 +174,7 @@ def cpu_baseline(name: str, target_s: float = 12.0) -> dict:
                        depth=depth_s, sid_seed=spec.sid_seed, rho=spec.rho)
         pts, sid = s.points(), s.sids()
         t0 = time.perf_counter()
-        t = oracle.build_tree(pts, r=s.r, subset_mode=s.subset_mode, sid=sid, depth=depth_s, key_rule=s.key_rule)
+        t = oracle_build(oracle, spec, pts, sid, s, depth_s)
         dt = time.perf_counter() - t0
         if dt * 4 > target_s or n_s >= full_n:
             return {"value": n_s * t.levels / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -184,12 +195,11 @@ def run_reference(args) -> None:
     s = W.TreeSpec(spec.name, n_s, spec.d, spec.dist, spec.seed, spec.r, spec.subset_mode, spec.key_rule,
                    depth=depth_s, sid_seed=spec.sid_seed, rho=spec.rho)
     pts, sid = s.points(), s.sids()
-    kw = dict(r=s.r, subset_mode=s.subset_mode, sid=sid, depth=depth_s, key_rule=s.key_rule)
     for _ in range(args.warmup):
-        oracle.build_tree(pts, **kw)
+        oracle_build(oracle, spec, pts, sid, s, depth_s)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        t = oracle.build_tree(pts, **kw)
+        t = oracle_build(oracle, spec, pts, sid, s, depth_s)
     dt = time.perf_counter() - t0
     value = args.steps * n_s * t.levels / dt
     sample = f"n={n_s} depth={depth_s} of the {spec.name} recipe per step"
@@ -355,7 +365,7 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c3s", "w6", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c3s", "w6", "w6f", "c4", "c5"])
     ap.add_argument("--trees", type=int, default=4096, help="c4: number of trees")
     ap.add_argument("--requests", type=int, default=20000, help="c5: number of requests")
     ap.add_argument("--load", type=float, default=0.7, help="c5: arrival rate / solo capacity")

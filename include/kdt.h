@@ -88,8 +88,17 @@ typedef struct kdt_params {
   int32_t depth;                 /* > 0: fixed depth (2^depth leaves); 0: leaf mode     */
   int32_t leaf_size;             /* leaf mode: cells with <= leaf_size points stop (>= 1) */
   int32_t max_levels;            /* leaf mode: output capacity, 2^max_levels leaves     */
-  int32_t reserved;              /* must be 0                                           */
+  int32_t fourier_j;             /* 0: the exact subset-median split (Sec. 2). 1..32: the  */
+                                 /* paper's estimator (Sec. 3): each split is the root of  */
+                                 /* Eq. (kd:eq:b) built from the cell's sums of the first  */
+                                 /* 2J+1 terms of Lemma 1's expansion (cyclic keys, depth  */
+                                 /* mode, every coordinate in (0,1); plain builds only;    */
+                                 /* subsets do not change its sums, so r and the ids are   */
+                                 /* ignored)                                               */
 } kdt_params;
+
+/* Largest fourier_j. */
+#define KDT_FOURIER_MAX_J 32
 
 /*
  * Bytes of device workspace kdt_build needs for these parameters on the

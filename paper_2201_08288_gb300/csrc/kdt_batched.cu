@@ -31,6 +31,7 @@ kdt_status plan_batch(const kdt_tree_desc* trees, int32_t num, BatchPlan* bp) {
   for (int32_t i = 0; i < num; ++i) {
     const kdt_status v = kdt::validate_params(&trees[i].params);
     if (v != KDT_OK) return v;
+    if (trees[i].params.fourier_j != 0) return KDT_ERR_INVALID_ARG;  // plain builds only
     bp->trees[i] = kdt::plan_tree(trees[i].params);
     needs.add(trees[i].params, bp->trees[i]);
   }

@@ -78,19 +78,35 @@ kdt_status validate_params(const kdt_params* p) {
     if (p->leaf_size < 1) return KDT_ERR_INVALID_ARG;
     if (p->max_levels < 0 || p->max_levels > KDT_MAX_LEVELS) return KDT_ERR_INVALID_ARG;
   }
-  if (p->reserved != 0) return KDT_ERR_INVALID_ARG;
+  if (p->fourier_j < 0 || p->fourier_j > KDT_FOURIER_MAX_J) return KDT_ERR_INVALID_ARG;
+  if (p->fourier_j > 0 && (p->key_rule != KDT_KEY_CYCLIC || p->depth == 0)) return KDT_ERR_INVALID_ARG;
   return KDT_OK;
 }
 
-TreePlan plan_tree(const kdt_params& p) {
+kdt_params effective_params(const kdt_params& p) {
+  kdt_params e = p;
+  if (p.fourier_j > 0) {  // the estimator's sums do not depend on the subsets
+    e.r = 1;
+    e.subset_mode = KDT_SUBSET_MOD;
+    e.subset_id8 = nullptr;
+    e.subset_id16 = nullptr;
+  }
+  return e;
+}
+
+TreePlan plan_tree(const kdt_params& p0) {
+  const kdt_params p = effective_params(p0);
   TreePlan t;
   const uint64_t n = (uint64_t)p.n;
   t.n = n;
   t.L_cap = p.depth > 0 ? p.depth : p.max_levels;
-  t.small_max = subtree_capacity(p.d);
+  // the estimator's splits come from the multi-CTA steps only (no subtree
+  // kernel); its cells keep index order (no presort), so no leaf sort either
+  const bool fourier = p.fourier_j > 0;
+  t.small_max = fourier ? 0 : subtree_capacity(p.d);
   t.sid_bytes = p.subset_mode == KDT_SUBSET_EXPLICIT ? (p.subset_id16 ? 2 : 1) : 0;
   const bool root_terminal = p.depth > 0 ? (n == 0) : (n <= (uint64_t)p.leaf_size);
-  t.leafsort = !root_terminal && p.subset_mode != KDT_SUBSET_CONTIGUOUS;
+  t.leafsort = !root_terminal && p.subset_mode != KDT_SUBSET_CONTIGUOUS && !fourier;
   t.presorted = t.leafsort && n > (uint64_t)t.small_max;
   t.huge_cap = t.leafsort ? n / (uint64_t)(kLeafBlockMax + 1) + 1 : 0;
   const uint64_t leaves = (uint64_t)1 << t.L_cap;
@@ -117,7 +133,9 @@ TreePlan plan_tree(const kdt_params& p) {
   return t;
 }
 
-void StepNeeds::add(const kdt_params& p, const TreePlan& tp) {
+void StepNeeds::add(const kdt_params& p0, const TreePlan& tp) {
+  const kdt_params p = effective_params(p0);
+  fourier = fourier || p.fourier_j > 0;
   points += tp.n;
   maxB += tp.maxB;
   cap_small += tp.cap_small;
@@ -160,7 +178,7 @@ StepPlan plan_step(const StepNeeds& needs) {
   s.tiles = take((size_t)s.max_tiles * sizeof(uint2));
   s.tile_left = take((size_t)s.max_tiles * 4);
   s.tile_loff = take((size_t)s.max_tiles * 4);
-  s.tile_mm = take(needs.widest ? (size_t)s.max_tiles * 2 * kMaxDims * 2 * 4 : 0);
+  s.tile_mm = take(needs.widest || needs.fourier ? (size_t)s.max_tiles * 2 * kMaxDims * 2 * 4 : 0);
   s.child_mm = take(needs.widest ? (size_t)s.maxB * 2 * kMaxDims * 2 * 4 : 0);
   s.kdim = take((size_t)s.maxB * 4);
   s.mkey = take((size_t)s.maxB * 4);
@@ -246,8 +264,9 @@ kdt_status Engine::reset() {
   return KDT_OK;
 }
 
-kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p, const TreePlan& tp,
+kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p0, const TreePlan& tp,
                          uint8_t* tb, uint32_t* out_perm, float* out_vals, int8_t* out_dims, int64_t* out_offs) {
+  const kdt_params p = effective_params(p0);
   const uint32_t mt = std::max<uint32_t>(plan_.needs.max_trees, 1);
   if (slot >= mt) return KDT_ERR_CAPACITY;
   TreeDev h{};
@@ -259,6 +278,7 @@ kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p
   h.depth = p.depth;
   h.leaf_size = p.leaf_size;
   h.max_levels = p.max_levels;
+  h.fourier_j = p.fourier_j;
   h.stall_limit = p.key_rule == KDT_KEY_CYCLIC ? p.d : 1;
   h.sid_bytes = tp.sid_bytes;
   h.small_max = tp.small_max;
@@ -366,7 +386,7 @@ kdt_status Engine::tick() {
     launch_big_step(trees_, s_, tiles_bound, (uint32_t)nseg_bound, plan_.bigseg_cap, has_roots, root_dims_,
                     plan_.needs.widest, plan_.needs.max_d,
                     plan_.needs.min_d == plan_.needs.max_d ? plan_.needs.max_d : 0, tune, big_points_,
-                    plan_.grid_sub, st_);
+                    plan_.grid_sub, st_, plan_.needs.fourier);
     ENGINE_TRY(cudaGetLastError());
     root_dims_ = false;
     uint32_t counts[4];
@@ -499,7 +519,7 @@ kdt_status Engine::record_tick(int p) {
   sd.warp_max = tune.warp_max;
   launch_big_step(trees_, sd, plan_.max_tiles, plan_.nseg_cap, plan_.bigseg_cap, false, false, plan_.needs.widest,
                   plan_.needs.max_d, plan_.needs.min_d == plan_.needs.max_d ? plan_.needs.max_d : 0, tune, 0,
-                  plan_.grid_sub, st_);
+                  plan_.grid_sub, st_, plan_.needs.fourier);
   ENGINE_TRY(cudaGetLastError());
   launch_subtree(trees_, small_, plan_.cap_small, words_ + W_SMALL, words_ + W_HEAD, slices_,
                  plan_.needs.slice_cells, plan_.grid_sub, 0, st_);

@@ -20,6 +20,9 @@
 namespace kdt {
 
 kdt_status validate_params(const kdt_params* p);
+// The parameters a build runs with: a Fourier-estimator build ignores the
+// subsets (one subset, no ids), since its statistics are sums.
+kdt_params effective_params(const kdt_params& p);
 
 // Memory of one tree (offsets relative to the tree's base, 256-byte aligned).
 struct TreePlan {
@@ -45,6 +48,7 @@ struct StepNeeds {
   uint64_t points = 0, maxB = 0, cap_small = 0, nseg = 0;
   uint32_t max_trees = 0, slice_cells = 32;
   bool widest = false;
+  bool fourier = false;  // a tree splits by the Fourier-moment estimator
   int max_d = 1, min_d = 1 << 30;  // min_d == max_d: every tree has the same d
   void add(const kdt_params& p, const TreePlan& tp);
 };

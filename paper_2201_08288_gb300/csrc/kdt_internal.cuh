@@ -78,7 +78,7 @@ struct TreeDev {
   uint32_t* huge;        // [huge_cap] terminal records too large for one CTA's leaf sort
   uint32_t* huge_count;  // device word
   uint32_t huge_cap;
-  uint32_t pad2;
+  int32_t fourier_j;     // > 0: splits by the Fourier-moment estimator with this many harmonics
   uint32_t* out_perm;
   float* out_vals;
   int8_t* out_dims;

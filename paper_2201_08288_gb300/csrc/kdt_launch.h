@@ -74,7 +74,7 @@ void launch_loop_cond(cudaGraphConditionalHandle h, const uint32_t* ncells_next,
                       cudaStream_t st);
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
                      uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d, int uniform_d,
-                     const SelectTuning& tune, uint64_t points, uint32_t sms, cudaStream_t st);
+                     const SelectTuning& tune, uint64_t points, uint32_t sms, cudaStream_t st, bool fourier = false);
 
 // Dynamic shared memory of the staged scatter (two CTAs per SM).
 constexpr uint32_t kScatterSmemBytes = 100 * 1024;

@@ -259,6 +259,7 @@ kdt_status kdt_server_submit(kdt_server* sv, const kdt_tree_desc* req, uint64_t*
   if (!sv || !req || !ticket) return KDT_ERR_INVALID_ARG;
   const kdt_status v = kdt::validate_params(&req->params);
   if (v != KDT_OK) return v;
+  if (req->params.fourier_j != 0) return KDT_ERR_INVALID_ARG;  // plain builds only
   const kdt_params& p = req->params;
   const int L_cap = p.depth > 0 ? p.depth : p.max_levels;
   if ((p.n > 0 && (!req->points || !req->out_perm)) || !req->out_node_offsets ||

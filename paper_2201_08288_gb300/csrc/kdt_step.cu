@@ -933,6 +933,214 @@ __global__ void __launch_bounds__(256, 1) k_combine_warp(const TreeDev* trees, S
   for (uint32_t c = blockIdx.x * 8u + (threadIdx.x >> 5); c < nc; c += gridDim.x * 8u) combine_warp_cell(trees, s, c);
 }
 
+// ------------------------------------------- the paper's estimator (Sec. 3)
+
+constexpr int kFourierTerms = 2 * KDT_FOURIER_MAX_J + 1;
+constexpr int kTileRecWords = 2 * kMaxDims * 2;  // words of a tile's record in tile_mm
+static_assert(kFourierTerms * 2 <= kTileRecWords, "a tile's sums fit its record");
+
+// The sums over a cell's points of the basis terms of Lemma 1 on its key
+// coordinate, c_0 = 1, c_{2j-1} = cos((2j-1)x), c_{2j} = sin((2j-1)x) for
+// j = 1..J (the additive statistics of Sec. 3.2). The kernel is persistent:
+// CTA k takes the tiles [k T / G, (k+1) T / G) of the step (T tiles, G
+// CTAs). Each thread holds 8 points of a tile and runs the odd harmonics
+// for all of them at once (h(k+2) = 2 cos(2x) h(k) - h(k-2), from one sincosf
+// per point), adding each harmonic's terms in float, then over the warp by
+// a shuffle tree in float (double arithmetic is scarce on this GPU); the CTA
+// adds the warps' sums in double in a fixed order into a running total per
+// term, written to the record of the run's first tile when the
+// CTA's run of the cell's tiles ends. The split kernel adds a cell's run
+// records in order, so the result does not depend on scheduling. A
+// coordinate outside (0,1) is reported.
+__global__ void __launch_bounds__(256, 2) k_fourier_moments(const TreeDev* trees, StepDev s) {
+  constexpr int kPer = kTile / 256;
+  __shared__ float red[8][kFourierTerms];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t ntiles = *s.ntiles_total;
+  const uint32_t t_begin = (uint32_t)(((uint64_t)blockIdx.x * ntiles) / gridDim.x);
+  const uint32_t t_end = (uint32_t)(((uint64_t)(blockIdx.x + 1) * ntiles) / gridDim.x);
+  double run = 0.0;  // thread j: term j of the current run
+  uint32_t run_first = t_begin;
+  for (uint32_t tile = t_begin; tile < t_end; ++tile) {
+    const uint2 tl = s.tiles[tile];
+    const Cell cell = s.cells[tl.x];
+    const TreeDev& t = trees[cell.tree];
+    const int J = t.fourier_j;
+    const float* X = (const float*)key_column(t, cell, s.kdim[tl.x]) + cell.begin;
+    const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
+    float c2[kPer], cp[kPer], sp[kPer], cc[kPer], sc[kPer];
+    bool outside = false, nan = false;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const uint32_t i = tl.y + threadIdx.x + 256u * q;
+      const bool ok = i < end;
+      const float x = ok ? __ldg(X + i) : 0.5f;
+      nan |= ok && x != x;
+      outside |= ok && !(x > 0.f && x < 1.f);
+      float sx, cx;
+      sincosf(x, &sx, &cx);
+      const float w = ok ? 1.f : 0.f;  // a missing point adds nothing
+      c2[q] = 2.f * (cx * cx - sx * sx);
+      cp[q] = w * cx;  // harmonic -1
+      sp[q] = -w * sx;
+      cc[q] = w * cx;  // harmonic 1
+      sc[q] = w * sx;
+      cnt += ok ? 1u : 0u;
+    }
+    if (outside) set_status(t, nan ? ST_NAN_INPUT : ST_INVALID_ARG);
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) red[warp][0] = (float)cnt;
+    for (int k = 1; k <= J; ++k) {
+      float ac = 0.f, as = 0.f;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        ac += cc[q];
+        as += sc[q];
+        const float cn = fmaf(c2[q], cc[q], -cp[q]), sn = fmaf(c2[q], sc[q], -sp[q]);
+        cp[q] = cc[q];
+        sp[q] = sc[q];
+        cc[q] = cn;
+        sc[q] = sn;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ac += __shfl_down_sync(0xffffffffu, ac, o);
+        as += __shfl_down_sync(0xffffffffu, as, o);
+      }
+      if (lane == 0) {
+        red[warp][2 * k - 1] = ac;
+        red[warp][2 * k] = as;
+      }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x <= 2 * J) {
+      double v = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) v += (double)red[w][threadIdx.x];
+      run += v;
+    }
+    // the CTA's run of this cell's tiles ends here: write its record
+    if (tile + 1 == t_end || s.tiles[tile + 1].x != tl.x) {
+      if ((int)threadIdx.x <= 2 * J) ((double*)(s.tile_mm + (size_t)run_first * kTileRecWords))[threadIdx.x] = run;
+      run = 0.0;
+      run_first = tile + 1;
+    }
+    __syncthreads();
+  }
+}
+
+// Per cell, one warp: the cell's sums C_j (its tiles' records added in tile
+// order; lane l holds terms l, l + 32, l + 64), its bounds (a, b) on its key
+// coordinate (the splits of its ancestors on that coordinate, (0,1) at the
+// root), and the root of Eq. (kd:eq:b) by 60 bisection steps in double on
+// (a, b) of F(m) = 1_J(a, m) - 1_J(m, b) = sum_j C_j (g_j(a, m) - g_j(m, b)),
+// with g_j of Lemma 1: the term of j = 0 is (1(b<1) - 1(a>0)) / 2, of
+// j = 2k-1 q (2 sin(Km) - 1(a>0) sin(Ka) - 1(b<1) sin(Kb)) and of j = 2k
+// q (1(a>0) cos(Ka) + 1(b<1) cos(Kb) - 2 cos(Km)), K = 2k-1, q = 2 / (pi K).
+// The lower end moves up while F < 0; the split is the last midpoint
+// rounded to float, and a point goes left when its coordinate is <= it. The
+// harmonics of the midpoint are evaluated in float (their error moves the
+// root by about 1e-7 of the cell's width), the sums in double.
+__global__ void __launch_bounds__(256) k_fourier_split(const TreeDev* trees, StepDev s, uint32_t mgrid) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nc = ncells_of(s);
+  const uint32_t ntiles = *s.ntiles_total;
+  auto range_start = [&](uint32_t k) { return (uint32_t)(((uint64_t)k * ntiles) / mgrid); };
+  for (uint32_t c = blockIdx.x * 8u + (threadIdx.x >> 5); c < nc; c += gridDim.x * 8u) {
+    const Cell cell = s.cells[c];
+    const TreeDev& t = trees[cell.tree];
+    const int nt = 2 * t.fourier_j + 1;
+    const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
+    // the moments kernel's runs of this cell start at tb and at every start
+    // of a CTA's tile range inside (tb, te)
+    uint64_t k0 = ((uint64_t)tb * mgrid) / (ntiles > 0u ? ntiles : 1u);
+    uint32_t k = (uint32_t)(k0 < (uint64_t)mgrid ? k0 : (uint64_t)(mgrid - 1u));
+    while (k > 0u && range_start(k) > tb) --k;
+    while (k + 1u < mgrid && range_start(k + 1u) <= tb) ++k;
+    double C[3] = {0.0, 0.0, 0.0};
+    uint32_t r0 = tb;
+    for (uint32_t kk = k + 1u;; ++kk) {
+      const double* rec = (const double*)(s.tile_mm + (size_t)r0 * kTileRecWords);
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (lane + 32 * q < nt) C[q] += rec[lane + 32 * q];
+      uint32_t nxt = te;
+      while (kk < mgrid && (nxt = range_start(kk)) <= r0) ++kk;  // CTAs with empty ranges
+      if (kk >= mgrid || nxt >= te) break;
+      r0 = nxt;
+    }
+    const uint32_t dim = s.kdim[c];
+    double a = 0.0, b = 1.0;
+    if (lane == 0)
+      for (uint32_t h = cell.heap; h > 0;) {
+        const uint32_t par = (h - 1u) / 2u;
+        const uint32_t plevel = 31u - (uint32_t)__clz(par + 1u);
+        if (plevel % (uint32_t)t.d == dim) {
+          const double v = (double)t.out_vals[par];
+          if (h == 2u * par + 1u)
+            b = fmin(b, v);
+          else
+            a = fmax(a, v);
+        }
+        h = par;
+      }
+    a = __shfl_sync(0xffffffffu, a, 0);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    const double ia = a > 0.0 ? 1.0 : 0.0, ib = b < 1.0 ? 1.0 : 0.0;
+    // per term: F_j(m) = base + slope * (sin or cos)(K m)
+    double base[3], slope[3], K[3];
+    bool use_sin[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int j = lane + 32 * q;
+      base[q] = slope[q] = 0.0;
+      K[q] = 0.0;
+      use_sin[q] = true;
+      if (j >= nt) continue;
+      if (j == 0) {
+        base[q] = C[q] * 0.5 * (ib - ia);
+        continue;
+      }
+      const double k = (double)(2 * ((j + 1) / 2) - 1);
+      const double qk = 2.0 / (3.14159265358979323846 * k);
+      K[q] = k;
+      if (j & 1) {
+        base[q] = -C[q] * qk * (ia * sin(k * a) + ib * sin(k * b));
+        slope[q] = 2.0 * C[q] * qk;
+      } else {
+        base[q] = C[q] * qk * (ia * cos(k * a) + ib * cos(k * b));
+        slope[q] = -2.0 * C[q] * qk;
+        use_sin[q] = false;
+      }
+    }
+    double lo = a, hi = b;
+    for (int it = 0; it < 60; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      double f = 0.0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (slope[q] != 0.0 || base[q] != 0.0)
+          f += base[q] + (slope[q] != 0.0
+                              ? slope[q] * (double)(use_sin[q] ? sinf((float)(K[q] * mid)) : cosf((float)(K[q] * mid)))
+                              : 0.0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+      f = __shfl_sync(0xffffffffu, f, 0);  // lane 0's sum decides for the warp
+      if (f < 0.0)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    if (lane == 0) {
+      const float m32 = (float)(0.5 * (lo + hi));
+      s.mkey[c] = ord_key(m32);
+      t.out_vals[cell.heap] = m32;
+      t.out_dims[cell.heap] = (int8_t)dim;
+    }
+  }
+}
+
 // ------------------------------------------------------------ partition
 
 // Per tile: number of points with key <= split. One warp per tile: the
@@ -1139,7 +1347,7 @@ cudaError_t prepare_step_kernels() {
 
 void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t nseg,
                      uint32_t max_bigseg, bool has_roots, bool need_root_dims, bool any_widest, int max_d, int uniform_d,
-                     const SelectTuning& tune, uint64_t points, uint32_t sms, cudaStream_t st) {
+                     const SelectTuning& tune, uint64_t points, uint32_t sms, cudaStream_t st, bool fourier) {
   // s.ncells: the step's cells, or (s.ncells_dev set: a step inside a graph)
   // their capacity; per-cell kernels stride over the cells, so their grids
   // cover the cells exactly here and are capped there
@@ -1164,40 +1372,49 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
     { TraceScope ts(K_MINMAX, st, points); k_minmax<<<max_tiles, kTileThreads, 0, st>>>(trees, s); }
     { TraceScope ts(K_PICK_DIM, st); k_pick_dim<<<nc, 1024, 0, st>>>(trees, s); }
   }
-  { TraceScope ts(K_SEGS, st); k_segs<<<cells_grid(1, sms * 8u), 256, 0, st>>>(trees, s); }
-  {
-    TraceScope ts(K_SELECT_TINY, st, points);
-    k_select_tiny<<<std::max<uint32_t>(1, std::min<uint32_t>((nseg + 255) / 256, sms * 16u)), 256, 0, st>>>(trees, s);
-  }
-  {
-    TraceScope ts(K_SELECT_SMALL, st, points);
-    k_select_small<<<std::max<uint32_t>(1, std::min<uint32_t>((nseg + 7) / 8, sms * 8u)), 256, 0, st>>>(trees, s);
-  }
-  if (max_bigseg) {
-    TraceScope ts(K_SELECT_BIG, st);
-    const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>(max_bigseg, sms * 4u));
-    if (tune.cta_threads == 512) {
-      if (tune.digit_bits == 8)
-        k_select_big<512, 8><<<grid, 512, 0, st>>>(trees, s);
-      else
-        k_select_big<512, 11><<<grid, 512, 0, st>>>(trees, s);
-    } else {
-      if (tune.digit_bits == 8)
-        k_select_big<256, 8><<<grid, 256, 0, st>>>(trees, s);
-      else
-        k_select_big<256, 11><<<grid, 256, 0, st>>>(trees, s);
-    }
-  }
   // a CTA per cell while cells are few (large subset counts, deep scans),
   // a warp per cell once they are many (and in a graph, where the count is
   // not known when the launch is recorded)
   const bool many = dev || nc >= kManyCells;
-  {
-    TraceScope ts(K_COMBINE, st);
-    if (many)
-      k_combine_warp<<<cells_grid(8, sms * 8u), 256, 0, st>>>(trees, s);
-    else
-      k_combine<<<nc, 256, 0, st>>>(trees, s);
+  if (fourier) {  // the paper's estimator: per-run sums, then the root per cell
+    const uint32_t mgrid = std::max<uint32_t>(1, std::min(max_tiles, sms * 2u));
+    {
+      TraceScope ts(K_FOURIER_MOMENTS, st, points);
+      k_fourier_moments<<<mgrid, 256, 0, st>>>(trees, s);
+    }
+    { TraceScope ts(K_FOURIER_SPLIT, st); k_fourier_split<<<cells_grid(8, sms * 8u), 256, 0, st>>>(trees, s, mgrid); }
+  } else {
+    { TraceScope ts(K_SEGS, st); k_segs<<<cells_grid(1, sms * 8u), 256, 0, st>>>(trees, s); }
+    {
+      TraceScope ts(K_SELECT_TINY, st, points);
+      k_select_tiny<<<std::max<uint32_t>(1, std::min<uint32_t>((nseg + 255) / 256, sms * 16u)), 256, 0, st>>>(trees, s);
+    }
+    {
+      TraceScope ts(K_SELECT_SMALL, st, points);
+      k_select_small<<<std::max<uint32_t>(1, std::min<uint32_t>((nseg + 7) / 8, sms * 8u)), 256, 0, st>>>(trees, s);
+    }
+    if (max_bigseg) {
+      TraceScope ts(K_SELECT_BIG, st);
+      const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>(max_bigseg, sms * 4u));
+      if (tune.cta_threads == 512) {
+        if (tune.digit_bits == 8)
+          k_select_big<512, 8><<<grid, 512, 0, st>>>(trees, s);
+        else
+          k_select_big<512, 11><<<grid, 512, 0, st>>>(trees, s);
+      } else {
+        if (tune.digit_bits == 8)
+          k_select_big<256, 8><<<grid, 256, 0, st>>>(trees, s);
+        else
+          k_select_big<256, 11><<<grid, 256, 0, st>>>(trees, s);
+      }
+    }
+    {
+      TraceScope ts(K_COMBINE, st);
+      if (many)
+        k_combine_warp<<<cells_grid(8, sms * 8u), 256, 0, st>>>(trees, s);
+      else
+        k_combine<<<nc, 256, 0, st>>>(trees, s);
+    }
   }
   {
     TraceScope ts(K_PART_COUNT, st, points);

@@ -60,7 +60,7 @@ class kdt_params(ctypes.Structure):
         ("depth", ctypes.c_int32),
         ("leaf_size", ctypes.c_int32),
         ("max_levels", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("fourier_j", ctypes.c_int32),
     ]
 
 
@@ -85,6 +85,8 @@ class kdt_tuning(ctypes.Structure):
     _fields_ = [("tiny_max", ctypes.c_int32), ("bitonic_max", ctypes.c_int32), ("warp_max", ctypes.c_int32),
                 ("cta_threads", ctypes.c_int32), ("digit_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
+
+KDT_FOURIER_MAX_J = 32  # largest fourier_j
 
 TUNING_FIELDS = ("tiny_max", "bitonic_max", "warp_max", "cta_threads", "digit_bits")
 # the choices kdt_set_tuning accepts, per field
@@ -157,12 +159,12 @@ def load_library(path: str = LIB_PATH):
 
 def make_params(n: int, d: int, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid_ptr: int = 0,
                 sid_bytes: int = 1, depth: int = 0, leaf_size: int = 1, max_levels: int = 20,
-                key_rule: int = KDT_KEY_CYCLIC) -> kdt_params:
+                key_rule: int = KDT_KEY_CYCLIC, fourier_j: int = 0) -> kdt_params:
     p = kdt_params()
     p.n, p.d, p.subset_mode, p.r, p.key_rule = n, d, subset_mode, r, key_rule
     p.subset_id8 = sid_ptr if (sid_ptr and sid_bytes == 1) else None
     p.subset_id16 = sid_ptr if (sid_ptr and sid_bytes == 2) else None
-    p.depth, p.leaf_size, p.max_levels, p.reserved = depth, leaf_size, max_levels, 0
+    p.depth, p.leaf_size, p.max_levels, p.fourier_j = depth, leaf_size, max_levels, fourier_j
     return p
 
 
@@ -233,18 +235,20 @@ def _sid_info(sid):
 
 def kdt_build(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None, depth: int = 0,
               leaf_size: int = 1, max_levels: int = 20, key_rule: int = KDT_KEY_CYCLIC,
-              workspace=None, stream=None, outputs: Optional[Tree] = None) -> Tree:
+              workspace=None, stream=None, outputs: Optional[Tree] = None, fourier_j: int = 0) -> Tree:
     """Build on the device. points: torch float32 CUDA tensor [d, n], contiguous.
     sid: uint8 (or int16 holding uint16) CUDA tensor [n] for explicit subsets.
     workspace: optional uint8 CUDA tensor of >= kdt_workspace_size bytes.
-    outputs: optional preallocated Tree of tensors (sized for the capacity)."""
+    outputs: optional preallocated Tree of tensors (sized for the capacity).
+    fourier_j > 0: splits by the paper's Fourier-moment estimator with J
+    harmonics (cyclic keys, depth mode, coordinates in (0,1))."""
     import torch
     if not (points.is_cuda and points.dtype == torch.float32 and points.is_contiguous() and points.dim() == 2):
         raise ValueError("points must be a contiguous float32 CUDA tensor [d, n]")
     d, n = points.shape
     sid_ptr, sid_bytes = _sid_info(sid)
     p = make_params(n, d, r=r, subset_mode=subset_mode, sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth,
-                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule)
+                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule, fourier_j=fourier_j)
     lib = load_library()
     cap = _capacity(depth, max_levels)
     dev = points.device
@@ -272,7 +276,7 @@ def kdt_build(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None
 
 def kdt_build_host(points: np.ndarray, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None,
                    depth: int = 0, leaf_size: int = 1, max_levels: int = 20, key_rule: int = KDT_KEY_CYCLIC,
-                   workspace=None, stream=None, outputs=None) -> Tree:
+                   workspace=None, stream=None, outputs=None, fourier_j: int = 0) -> Tree:
     """Build from HOST arrays (numpy, ideally pinned): copies in, builds, copies
     the outputs back into numpy arrays, all inside the library call."""
     import torch
@@ -283,7 +287,7 @@ def kdt_build_host(points: np.ndarray, *, r: int = 1, subset_mode: int = KDT_SUB
         sid = np.ascontiguousarray(sid)
         sid_ptr, sid_bytes = sid.ctypes.data, sid.dtype.itemsize
     p = make_params(n, d, r=r, subset_mode=subset_mode, sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth,
-                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule)
+                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule, fourier_j=fourier_j)
     cap = _capacity(depth, max_levels)
     if outputs is None:
         outputs = Tree(np.empty(max(n, 1), np.uint32), np.empty(max((1 << cap) - 1, 1), np.float32),

@@ -62,6 +62,20 @@ def mvn_common_corr(n: int, d: int, rho: float, seed: int) -> np.ndarray:
     return (chol @ z).astype(np.float32)
 
 
+def mvn_probit(n: int, d: int, rho: float, seed: int) -> np.ndarray:
+    """Host version of mvn_probit_device's recipe (a different random stream)."""
+    from scipy.special import ndtr
+    z = mvn_common_corr(n, d, rho, seed).astype(np.float64)
+    return np.clip(ndtr(z), 2.0 ** -24, 1.0 - 2.0 ** -24).astype(np.float32)
+
+
+def uniform_open(n: int, d: int, seed: int) -> np.ndarray:
+    """Uniform on the open cube (0,1)^d: k / 2^24 with k uniform on
+    1 .. 2^24 - 1 (exact in float32, never 0 or 1)."""
+    rng = np.random.default_rng(seed)
+    return (rng.integers(1, 1 << 24, size=(d, n)) / float(1 << 24)).astype(np.float32)
+
+
 def explicit_sids(n: int, r: int, seed: int) -> np.ndarray:
     """Subset ids uniform on [0, r); uint8 when r <= 256 else uint16."""
     rng = np.random.default_rng(seed)
@@ -129,6 +143,28 @@ def mvn_common_corr_device(n: int, d: int, rho: float, seed: int, device="cuda")
     return out
 
 
+def uniform_open_device(n: int, d: int, seed: int, device="cuda"):
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    k = torch.randint(1, 1 << 24, (d, n), generator=g, device=device, dtype=torch.int32)
+    return k.to(torch.float32) / float(1 << 24)
+
+
+def mvn_probit_device(n: int, d: int, rho: float, seed: int, device="cuda"):
+    """Sec. 5's trivariate normal mapped into (0,1)^d coordinate by coordinate
+    by the standard normal CDF (in float64), clamped to [2^-24, 1 - 2^-24]."""
+    import torch
+    x = mvn_common_corr_device(n, d, rho, seed, device)
+    out = torch.empty_like(x)
+    step = 1 << 24
+    lo, hi = 2.0 ** -24, 1.0 - 2.0 ** -24
+    for b in range(0, n, step):
+        e = min(n, b + step)
+        z = x[:, b:e].to(torch.float64)
+        out[:, b:e] = (0.5 * torch.erfc(-z / np.sqrt(2.0))).clamp_(lo, hi).to(torch.float32)
+    return out
+
+
 def explicit_sids_device(n: int, r: int, seed: int, device="cuda"):
     import torch
     g = torch.Generator(device=device).manual_seed(seed)
@@ -155,6 +191,7 @@ class TreeSpec:
     max_levels: int = 24
     sid_seed: Optional[int] = None
     rho: float = 0.0
+    fourier_j: int = 0        # > 0: the Fourier-moment estimator with J harmonics
     extra: dict = field(default_factory=dict)
 
     def points(self) -> np.ndarray:
@@ -168,6 +205,10 @@ class TreeSpec:
             return student_t_snapped(self.n, self.d, 3.0, 0.1, 256, self.seed)
         if self.dist == "mvn":
             return mvn_common_corr(self.n, self.d, self.rho, self.seed)
+        if self.dist == "uniform_open":
+            return uniform_open(self.n, self.d, self.seed)
+        if self.dist == "mvn_probit":
+            return mvn_probit(self.n, self.d, self.rho, self.seed)
         raise ValueError(self.dist)
 
     def points_device(self, device="cuda"):
@@ -181,6 +222,10 @@ class TreeSpec:
             return student_t_snapped_device(self.n, self.d, 3.0, 0.1, 256, self.seed, device)
         if self.dist == "mvn":
             return mvn_common_corr_device(self.n, self.d, self.rho, self.seed, device)
+        if self.dist == "uniform_open":
+            return uniform_open_device(self.n, self.d, self.seed, device)
+        if self.dist == "mvn_probit":
+            return mvn_probit_device(self.n, self.d, self.rho, self.seed, device)
         raise ValueError(self.dist)
 
     def sids(self):
@@ -214,6 +259,14 @@ def config3(n: int = 1 << 27, depth: int = 20) -> TreeSpec:
     explicit subsets, widest-spread keys, depth 20."""
     return TreeSpec(f"plain_studentt_n{n}_d8_r256explicit_widest_depth{depth}", n, 8, "student_t", 0,
                     256, 2, 1, depth=depth, sid_seed=1)
+
+
+def paper_mvn_fourier(n: int, rho: float, depth: int, J: int, seed: int = 0) -> TreeSpec:
+    """Sec. 5's shape for the paper's own estimator: the trivariate normal with
+    common correlation rho mapped into (0,1)^3 by the normal CDF, cyclic keys,
+    splits by the Fourier-moment estimator with J harmonics."""
+    return TreeSpec(f"paper_mvn_fourier_rho{rho}_n{n}_depth{depth}_J{J}", n, 3, "mvn_probit", seed, 1, 0, 0,
+                    depth=depth, rho=rho, fourier_j=J)
 
 
 def leaf_mode_levels(n: int) -> int:

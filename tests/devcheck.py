@@ -32,10 +32,13 @@ def ord_key(bits: torch.Tensor) -> torch.Tensor:
 
 
 def check_tree_device(pts: torch.Tensor, perm: torch.Tensor, vals: torch.Tensor, dims: torch.Tensor,
-                      offs: torch.Tensor, L: int, key_rule: int, depth_mode: bool = True) -> None:
+                      offs: torch.Tensor, L: int, key_rule: int, depth_mode: bool = True,
+                      fourier: bool = False) -> None:
     """Raises AssertionError on the first violated property. pts: float32
     [d, n] on any device; perm int32/int64 [n]; vals float32 [2^L - 1]; dims
-    int8 [2^L - 1]; offs int64 [2^L + 1]."""
+    int8 [2^L - 1]; offs int64 [2^L + 1]. fourier: the splits are the
+    Fourier estimator's roots, not keys of their nodes (no key-of-node and
+    quartile checks)."""
     dev = pts.device
     d, n = pts.shape
     perm = perm[:n].to(torch.int64)
@@ -85,9 +88,10 @@ def check_tree_device(pts: torch.Tensor, perm: torch.Tensor, vals: torch.Tensor,
         split = ldims >= 0
         if depth_mode:
             assert torch.equal(split, W > 0), f"level {l}: a non-empty node without a split, or an empty one with"
-        assert bool((n_eq[split] > 0).all()), f"level {l}: a split key is not a key of its node"
-        assert bool((4 * n_le[split] >= W[split]).all()), f"level {l}: fewer than ceil(W/4) keys <= split"
-        assert bool((4 * n_ge[split] > W[split]).all()), f"level {l}: no more than W/4 keys >= split"
+        if not fourier:
+            assert bool((n_eq[split] > 0).all()), f"level {l}: a split key is not a key of its node"
+            assert bool((4 * n_le[split] >= W[split]).all()), f"level {l}: fewer than ceil(W/4) keys <= split"
+            assert bool((4 * n_ge[split] > W[split]).all()), f"level {l}: no more than W/4 keys >= split"
         if key_rule == 0:
             assert bool((ldims[split] == l % d).all()), f"level {l}: not the cyclic coordinate"
         else:
@@ -133,3 +137,35 @@ def check_sampled_nodes(spec, pts_h, sid_h, perm, vals, dims, offs, L, levels, s
         assert np.float32(val).view(np.uint32) == vals[h].view(np.uint32), \
             f"node {h} (level {level}): split {vals[h]!r}, oracle {val!r}"
         assert left == le - lb, f"node {h} (level {level}): left count {le - lb}, oracle {left}"
+
+
+def fourier_node_tolerance(a: float, b: float) -> float:
+    """Bound on |GPU root - oracle root| for one node: the GPU sums float32
+    basis terms (|error| about 1e-7 per term, 5e-6 per point with the thread
+    sums), which moves F by at most about W * 6e-5 while F rises by about
+    2W / (b - a) per unit of m, i.e. 3e-5 (b - a); with margin 1e-4 (b - a),
+    plus the float rounding of the split."""
+    return 1e-4 * (b - a) + 1e-6
+
+
+def check_fourier_nodes(pts_h, perm, vals, dims, offs, L, J, heaps):
+    """For each node of `heaps`: the oracle's root of Eq. (kd:eq:b) from the
+    points the GPU put in the node and the bounds its ancestors' splits give
+    it, against the GPU's split, within fourier_node_tolerance."""
+    d = pts_h.shape[0]
+    worst = 0.0
+    for h in heaps:
+        b0, e0, level = treecheck.node_range(offs, L, h)
+        if e0 == b0:
+            assert int(dims[h]) == -1 and np.isposinf(vals[h]), f"node {h}: empty node without the sentinel"
+            continue
+        t = level % d
+        assert int(dims[h]) == t, f"node {h}: dim {dims[h]}, want {t}"
+        a, b = oracle.fourier_cell_bounds(vals, h, d)
+        x = pts_h[t, np.asarray(perm[b0:e0], dtype=np.int64)].astype(np.float64)
+        assert np.all(x > a) and np.all(x <= b), f"node {h}: points outside its bounds"
+        m = oracle.fourier_split(x, a, b, J)
+        err = abs(float(vals[h]) - m)
+        worst = max(worst, err / (b - a))
+        assert err <= fourier_node_tolerance(a, b), f"node {h} (level {level}): split {vals[h]!r}, oracle {m!r}"
+    return worst
