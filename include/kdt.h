@@ -118,13 +118,15 @@ kdt_status kdt_workspace_size(const kdt_params *p, size_t *bytes);
  *   out_perm         device [n]: original index of the point at each position of
  *                    the final order (leaves in order, increasing index inside).
  *   out_split_vals   device [2^L - 1]: split value of each node in level order
- *                    (bit-identical to a coordinate of the node's points).
+ *                    (bit-identical to a coordinate of the node's points; with
+ *                    fourier_j > 0 the estimator's root rounded to float).
  *   out_split_dims   device [2^L - 1]: split coordinate, -1 for sentinels.
  *   out_node_offsets device [2^L + 1]: leaf k holds out_perm[offs[k]..offs[k+1]).
  *   out_levels       host: L, the number of split levels built (depth, or the
  *                    leaf-mode result). Capacity: outputs must hold
  *                    2^depth (depth mode) or 2^max_levels (leaf mode) leaves.
- * Errors: KDT_ERR_INVALID_ARG, KDT_ERR_NAN_INPUT, KDT_ERR_LEVEL_CAP,
+ * Errors: KDT_ERR_INVALID_ARG (also: fourier_j > 0 and a coordinate outside the
+ *         open interval (0,1)), KDT_ERR_NAN_INPUT, KDT_ERR_LEVEL_CAP,
  *         KDT_ERR_CAPACITY (workspace too small), KDT_ERR_OOM, KDT_ERR_CUDA.
  */
 kdt_status kdt_build(const float *points, const kdt_params *p, void *workspace,
