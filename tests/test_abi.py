@@ -59,7 +59,8 @@ def test_status_strings_and_capacity_need_no_gpu(lib):
 
 
 @pytest.mark.parametrize("kw", [dict(r=0), dict(r=4097), dict(depth=31), dict(depth=0, leaf_size=0),
-                                dict(key_rule=3)])
+                                dict(key_rule=3), dict(fourier_j=33), dict(fourier_j=-1),
+                                dict(fourier_j=4, key_rule=1), dict(fourier_j=4, depth=0, leaf_size=8)])
 def test_invalid_params_rejected_on_host(lib, kw):
     from paper_2201_08288_gb300 import kdt
     args = dict(r=2, depth=3)
@@ -110,3 +111,15 @@ def test_tuning_set_get_and_validation_need_no_gpu(lib):
         assert lib.kdt_get_tuning(None) == 1
     finally:
         kdt.set_tuning(None)
+
+
+def test_estimator_workspace_ignores_the_subsets(lib):
+    """With fourier_j > 0 the build runs with one subset and no ids (the
+    estimator's statistics are sums), so r and the ids do not change the
+    workspace it needs; the median rule's workspace does depend on r."""
+    from paper_2201_08288_gb300 import kdt
+    base = kdt.kdt_workspace_size(kdt.make_params(100000, 3, depth=8, fourier_j=8))
+    for kw in (dict(r=64), dict(r=300, subset_mode=1), dict(r=16, subset_mode=2, sid_ptr=4096, sid_bytes=1)):
+        assert kdt.kdt_workspace_size(kdt.make_params(100000, 3, depth=8, fourier_j=8, **kw)) == base
+    assert kdt.kdt_workspace_size(kdt.make_params(100000, 3, depth=8, r=64)) > base
+
