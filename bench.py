@@ -46,6 +46,8 @@ def workload(name: str, rank: int):
         spec = W.paper_mvn(1 << 27, 0.5, 10)
     elif name == "w6f":  # the same shape through the normal CDF, split by the paper's estimator (J = 16)
         spec = W.paper_mvn_fourier(1 << 27, 0.5, 10, 16)
+    elif name == "w6fs":  # its profiling case: n=2^22, depth 8 (larger than L2, small for ncu)
+        spec = W.paper_mvn_fourier(1 << 22, 0.5, 8, 16)
     else:
         raise SystemExit(f"unknown workload {name}")
     spec.seed += 1000 * rank
@@ -365,7 +367,7 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c3s", "w6", "w6f", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c3s", "w6", "w6f", "w6fs", "c4", "c5"])
     ap.add_argument("--trees", type=int, default=4096, help="c4: number of trees")
     ap.add_argument("--requests", type=int, default=20000, help="c5: number of requests")
     ap.add_argument("--load", type=float, default=0.7, help="c5: arrival rate / solo capacity")
