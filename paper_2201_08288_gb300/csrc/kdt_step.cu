@@ -959,23 +959,42 @@ __global__ void __launch_bounds__(256, 2) k_fourier_moments(const TreeDev* trees
   const uint32_t ntiles = *s.ntiles_total;
   const uint32_t t_begin = (uint32_t)(((uint64_t)blockIdx.x * ntiles) / gridDim.x);
   const uint32_t t_end = (uint32_t)(((uint64_t)(blockIdx.x + 1) * ntiles) / gridDim.x);
+  // a tile's record, cell and this thread's points (loaded one tile ahead)
+  struct Ahead {
+    uint2 tl;
+    int32_t tree;
+    uint32_t end;
+    float x[kPer];
+  };
+  auto fetch = [&](uint32_t tile, Ahead& a) {
+    a.tl = s.tiles[tile];
+    const Cell cell = s.cells[a.tl.x];
+    const TreeDev& t = trees[cell.tree];
+    const float* X = (const float*)key_column(t, cell, s.kdim[a.tl.x]) + cell.begin;
+    a.tree = cell.tree;
+    a.end = min(a.tl.y + (uint32_t)kTile, cell.count);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const uint32_t i = a.tl.y + threadIdx.x + 256u * q;
+      a.x[q] = i < a.end ? __ldg(X + i) : 0.5f;
+    }
+  };
   double run = 0.0;  // thread j: term j of the current run
   uint32_t run_first = t_begin;
+  Ahead cur, nxt;
+  if (t_begin < t_end) fetch(t_begin, cur);
   for (uint32_t tile = t_begin; tile < t_end; ++tile) {
-    const uint2 tl = s.tiles[tile];
-    const Cell cell = s.cells[tl.x];
-    const TreeDev& t = trees[cell.tree];
+    if (tile + 1 < t_end) fetch(tile + 1, nxt);  // in flight while this tile is summed
+    const TreeDev& t = trees[cur.tree];
     const int J = t.fourier_j;
-    const float* X = (const float*)key_column(t, cell, s.kdim[tl.x]) + cell.begin;
-    const uint32_t end = min(tl.y + (uint32_t)kTile, cell.count);
     float c2[kPer], cp[kPer], sp[kPer], cc[kPer], sc[kPer];
     bool outside = false, nan = false;
     uint32_t cnt = 0;
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
-      const uint32_t i = tl.y + threadIdx.x + 256u * q;
-      const bool ok = i < end;
-      const float x = ok ? __ldg(X + i) : 0.5f;
+      const uint32_t i = cur.tl.y + threadIdx.x + 256u * q;
+      const bool ok = i < cur.end;
+      const float x = cur.x[q];
       nan |= ok && x != x;
       outside |= ok && !(x > 0.f && x < 1.f);
       float sx, cx;
@@ -1021,12 +1040,13 @@ __global__ void __launch_bounds__(256, 2) k_fourier_moments(const TreeDev* trees
       run += v;
     }
     // the CTA's run of this cell's tiles ends here: write its record
-    if (tile + 1 == t_end || s.tiles[tile + 1].x != tl.x) {
+    if (tile + 1 == t_end || nxt.tl.x != cur.tl.x) {
       if ((int)threadIdx.x <= 2 * J) ((double*)(s.tile_mm + (size_t)run_first * kTileRecWords))[threadIdx.x] = run;
       run = 0.0;
       run_first = tile + 1;
     }
     __syncthreads();
+    cur = nxt;
   }
 }
 
