@@ -81,6 +81,17 @@ def model_bytes_per_point_level(d: int, sid_bytes: int, subset_mode: int) -> flo
     return 4 + s_sel + 8 * (d + 1) + 2 * (sid_bytes if subset_mode == 2 else 0)
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's);
+    x itself when there is no process group."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class Clocks:
     """nvidia-smi sampler running during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -447,10 +458,7 @@ def main() -> None:
     ms = e0.elapsed_time(e1)
     launches = kdt.kdt_launch_count() - launches0
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     units = world * args.steps * spec.n * levels
     value = units / (ms / 1e3)
 
@@ -515,10 +523,7 @@ def main() -> None:
         if dist:
             dist.barrier()
         e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_s = float(t.item())
+        e_s = max_over_ranks(e_s, dist, dev)
         nleaf = 1 << ht.levels
         e2e = {"value": world * args.steps * spec.n * ht.levels / e_s, "unit": UNIT,
                "h2d_bytes_per_step": spec.d * spec.n * 4 + spec.n * sid_bytes,
