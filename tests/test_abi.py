@@ -123,3 +123,17 @@ def test_estimator_workspace_ignores_the_subsets(lib):
         assert kdt.kdt_workspace_size(kdt.make_params(100000, 3, depth=8, fourier_j=8, **kw)) == base
     assert kdt.kdt_workspace_size(kdt.make_params(100000, 3, depth=8, r=64)) > base
 
+
+
+def test_batched_builds_refuse_the_estimator(lib):
+    """The trees of a batched (or served) build share one select path, so the
+    estimator is a plain-build option; the refusal happens on the host."""
+    from paper_2201_08288_gb300 import kdt
+    descs = (kdt.kdt_tree_desc * 2)()
+    for i, j in enumerate((0, 6)):
+        descs[i].params = kdt.make_params(5000, 3, depth=6, fourier_j=j)
+    with pytest.raises(kdt.KdtError) as e:
+        kdt.kdt_workspace_size_batched(descs)
+    assert e.value.status == 1
+    descs[1].params = kdt.make_params(5000, 3, depth=6)
+    assert kdt.kdt_workspace_size_batched(descs) > 0
