@@ -92,3 +92,44 @@ def test_sampled_node_check_accepts_the_oracles_trees(mode):
     with pytest.raises(AssertionError):
         check_sampled_nodes(spec, pts, sid, t.perm, vals, t.split_dims, t.node_offsets, t.levels,
                             [2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2], seed=1)
+
+
+def _fourier_case():
+    from paper_2201_08288_gb300 import workloads
+    pts = workloads.uniform_open(4000, 2, seed=21)
+    return pts, oracle.fourier_build_tree(pts, depth=6, J=8)
+
+
+def test_fourier_checks_accept_the_oracles_tree():
+    from devcheck import check_fourier_nodes
+    pts, t = _fourier_case()
+    _check_f(pts, t.perm, t.split_vals, t.split_dims, t.node_offsets, t.levels)
+    worst = check_fourier_nodes(pts, t.perm, t.split_vals, t.split_dims, t.node_offsets, t.levels, 8, range(63))
+    assert worst < 1e-6
+
+
+def _check_f(pts, perm, vals, dims, offs, L):
+    check_tree_device(torch.from_numpy(pts), torch.from_numpy(perm.astype(np.int64)), torch.from_numpy(vals),
+                      torch.from_numpy(dims), torch.from_numpy(offs), L, 0, fourier=True)
+
+
+@pytest.mark.parametrize("mistake", ["split_off_by_a_thousandth", "split_dim", "perm_swap_across", "offset"])
+def test_fourier_checks_catch_planted_mistakes(mistake):
+    from devcheck import check_fourier_nodes
+    pts, t = _fourier_case()
+    perm, vals = t.perm.copy(), t.split_vals.copy()
+    dims, offs = t.split_dims.copy(), t.node_offsets.copy()
+    h = 5
+    if mistake == "split_off_by_a_thousandth":
+        a, b = oracle.fourier_cell_bounds(vals, h, 2)
+        vals[h] = np.float32(vals[h] + 1e-3 * (b - a))
+    elif mistake == "split_dim":
+        dims[h] = 1 - dims[h]
+    elif mistake == "perm_swap_across":
+        perm[0], perm[-1] = perm[-1], perm[0]
+    else:
+        k = int(np.argmax(np.diff(offs) >= 2))
+        offs[k + 1] += 1
+    with pytest.raises(AssertionError):
+        _check_f(pts, perm, vals, dims, offs, t.levels)
+        check_fourier_nodes(pts, perm, vals, dims, offs, t.levels, 8, range(63))
