@@ -35,8 +35,9 @@
  * Conventions: every pointer argument marked "device" is a CUDA device
  * pointer owned by the caller; the library never frees it. Calls are issued
  * on `stream` (a cudaStream_t; NULL = legacy default stream) and return after
- * the build has finished (the status needs one synchronisation). No function
- * allocates device memory except where stated.
+ * the build has finished: the host waits on the stream while a build runs
+ * (it reads the next level's cell counts between levels) and once at its end
+ * (the status). No function allocates device memory except where stated.
  */
 #ifndef KDT_H
 #define KDT_H
@@ -58,7 +59,8 @@ typedef enum kdt_status {
   KDT_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                           */
   KDT_ERR_LEVEL_CAP = 7,   /* leaf mode needs more than max_levels levels             */
   KDT_ERR_BUSY = 8,        /* the server cannot take the request now                  */
-  KDT_ERR_NOT_FOUND = 9    /* unknown server ticket                                   */
+  KDT_ERR_NOT_FOUND = 9,   /* unknown server ticket                                   */
+  KDT_ERR_CANCELLED = 10   /* the server request was cancelled before it ran          */
 } kdt_status;
 
 typedef enum kdt_key_rule { KDT_KEY_CYCLIC = 0, KDT_KEY_WIDEST_SPREAD = 1 } kdt_key_rule;
@@ -195,6 +197,7 @@ typedef struct kdt_server_info {
   uint64_t submitted, admitted, completed, ticks;
   int32_t in_flight, peak_in_flight;
   uint64_t arena_bytes, arena_bytes_in_use;
+  uint64_t cancelled, engine_failures;
 } kdt_server_info;
 
 /* Create a server on the current device. Errors: KDT_ERR_INVALID_ARG (budget
@@ -214,10 +217,22 @@ kdt_status kdt_server_submit(kdt_server *s, const kdt_tree_desc *request, uint64
  * KDT_ERR_BUSY: not finished yet. KDT_ERR_NOT_FOUND: unknown ticket. */
 kdt_status kdt_server_poll(kdt_server *s, uint64_t ticket, int32_t wait_ms, kdt_status *result,
                            int32_t *levels, double *latency_ms);
-/* Counters of the server (requests, ticks, occupancy). */
+/* Cancel a queued request: it is not built, and kdt_server_poll reports it
+ * finished with *result = KDT_ERR_CANCELLED. A request already admitted to the
+ * GPU (or finished) cannot be cancelled: KDT_ERR_BUSY (poll it as usual).
+ * KDT_ERR_NOT_FOUND: unknown or already released ticket. */
+kdt_status kdt_server_cancel(kdt_server *s, uint64_t ticket);
+/* Counters of the server (requests, ticks, occupancy, failures). */
 kdt_status kdt_server_stats(kdt_server *s, kdt_server_info *out);
 /* Finish the requests in flight, drop the queued ones, free the arena. */
 kdt_status kdt_server_destroy(kdt_server *s);
+/* Failure isolation. A build whose tree fails on the device (NaN input, level
+ * cap, a bounded wait that gave up) ends alone with that status; the other
+ * requests are unaffected. If a level step of the engine itself fails, every
+ * request on the GPU at that moment ends with the step's status and the
+ * engine's tables are cleared; queued requests then proceed. If the tables
+ * cannot be cleared (the device is unusable), every queued request ends with
+ * the status too, waiting pollers are woken, and later submits return it. */
 
 /* ---- tuning -------------------------------------------------------------
  * The lower median of every (cell, subset) segment (paper, Sec. 2: the
@@ -294,7 +309,9 @@ int32_t kdt_trace_read(kdt_kernel_stat *out, int32_t max, int32_t reset);
  *   KDT_ERR_CAPACITY (about one million 3-D points; fewer in higher d).
  *   The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture. Later calls reuse the address.
+ *   before any stream capture. Later calls reuse the address. Like
+ *   kdt_build, every call waits on its stream while it runs (see the
+ *   conventions at the top of this file).
  *   All calls on a device share the array: calls that overlap on the GPU (for
  *   example on two streams) race and produce garbage. Issue them in order.
  *   Arguments, outputs and errors are those of kdt_build (without workspace).
@@ -302,6 +319,39 @@ int32_t kdt_trace_read(kdt_kernel_stat *out, int32_t max, int32_t reset);
 kdt_status kdt_build_noalloc(const float *points, const kdt_params *p, uint32_t *out_perm,
                              float *out_split_vals, int8_t *out_split_dims,
                              int64_t *out_node_offsets, int32_t *out_levels, void *stream);
+
+/* ---- fault injection ----------------------------------------------------
+ * Host-side hooks that make a failure happen on purpose, so that the error
+ * paths can be tested without faulting a GPU. All are off by default; each
+ * kind holds a count of the events it still fails (0 = off).
+ *   KDT_FAULT_ALLOC        the library's next `count` device allocations
+ *                          (kdt_build, kdt_build_host, kdt_build_batched and
+ *                          kdt_autotune with a NULL workspace; the server's
+ *                          arena) fail as if the device were out of memory:
+ *                          the call returns KDT_ERR_OOM, having freed
+ *                          whatever it had allocated.
+ *   KDT_FAULT_SERVER_STEP  a server's next `count` level steps fail with
+ *                          KDT_ERR_CUDA before launching anything.
+ *   KDT_FAULT_SERVER_RESET the engine's next `count` table clears after a
+ *                          failed server step fail (the device counts as
+ *                          unusable for that server).
+ *   KDT_FAULT_WAIT         in the next `count` launches of the in-shared-memory
+ *                          subtree kernel, every CTA first waits on an
+ *                          mbarrier phase that nothing completes, with a
+ *                          bound of 1024 tries and no copy in flight; the wait
+ *                          gives up, the trees whose cells the launch held end
+ *                          with KDT_ERR_TIMEOUT, and the CTAs drain the rest of
+ *                          their queue without touching it.
+ * Errors: KDT_ERR_INVALID_ARG (unknown kind, count < 0). */
+typedef enum kdt_fault {
+  KDT_FAULT_ALLOC = 1,
+  KDT_FAULT_SERVER_STEP = 2,
+  KDT_FAULT_SERVER_RESET = 3,
+  KDT_FAULT_WAIT = 4
+} kdt_fault;
+kdt_status kdt_fault_inject(kdt_fault kind, int32_t count);
+/* Turn every fault kind off. */
+void kdt_fault_clear(void);
 
 /* Largest cell (points) the in-shared-memory subtree kernel takes for d
  * coordinates; larger cells are split by the multi-CTA level pipeline. */

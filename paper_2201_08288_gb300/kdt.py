@@ -27,14 +27,22 @@ KDT_MAX_SUBSETS = 4096
 
 STATUS_NAMES = {0: "KDT_OK", 1: "KDT_ERR_INVALID_ARG", 2: "KDT_ERR_NAN_INPUT", 3: "KDT_ERR_OOM",
                 4: "KDT_ERR_CUDA", 5: "KDT_ERR_CAPACITY", 6: "KDT_ERR_TIMEOUT", 7: "KDT_ERR_LEVEL_CAP",
-                8: "KDT_ERR_BUSY", 9: "KDT_ERR_NOT_FOUND"}
+                8: "KDT_ERR_BUSY", 9: "KDT_ERR_NOT_FOUND", 10: "KDT_ERR_CANCELLED"}
+KDT_ERR_CANCELLED = 10
+
+# fault kinds of kdt_fault_inject
+KDT_FAULT_ALLOC = 1
+KDT_FAULT_SERVER_STEP = 2
+KDT_FAULT_SERVER_RESET = 3
+KDT_FAULT_WAIT = 4
 
 # Every symbol include/kdt.h declares (checked by the CPU test suite).
 EXPORTED = ["kdt_workspace_size", "kdt_build", "kdt_workspace_size_host", "kdt_build_host",
             "kdt_subtree_capacity", "kdt_status_str", "kdt_trace_enable", "kdt_launch_count",
             "kdt_trace_read", "kdt_build_noalloc", "kdt_workspace_size_batched", "kdt_build_batched",
             "kdt_server_create", "kdt_server_submit", "kdt_server_poll", "kdt_server_stats",
-            "kdt_server_destroy", "kdt_tuning_default", "kdt_set_tuning", "kdt_get_tuning", "kdt_autotune"]
+            "kdt_server_destroy", "kdt_server_cancel", "kdt_tuning_default", "kdt_set_tuning", "kdt_get_tuning",
+            "kdt_autotune", "kdt_fault_inject", "kdt_fault_clear"]
 
 
 class KdtError(RuntimeError):
@@ -78,7 +86,8 @@ class kdt_tree_desc(ctypes.Structure):
 class kdt_server_info(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("ticks", ctypes.c_uint64), ("in_flight", ctypes.c_int32), ("peak_in_flight", ctypes.c_int32),
-                ("arena_bytes", ctypes.c_uint64), ("arena_bytes_in_use", ctypes.c_uint64)]
+                ("arena_bytes", ctypes.c_uint64), ("arena_bytes_in_use", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("engine_failures", ctypes.c_uint64)]
 
 
 class kdt_tuning(ctypes.Structure):
@@ -136,6 +145,12 @@ def load_library(path: str = LIB_PATH):
     lib.kdt_server_stats.restype = ctypes.c_int
     lib.kdt_server_destroy.argtypes = [vp]
     lib.kdt_server_destroy.restype = ctypes.c_int
+    lib.kdt_server_cancel.argtypes = [vp, ctypes.c_uint64]
+    lib.kdt_server_cancel.restype = ctypes.c_int
+    lib.kdt_fault_inject.argtypes = [ctypes.c_int, ctypes.c_int32]
+    lib.kdt_fault_inject.restype = ctypes.c_int
+    lib.kdt_fault_clear.argtypes = []
+    lib.kdt_fault_clear.restype = None
     lib.kdt_build_noalloc.argtypes = [vp, P, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), vp]
     lib.kdt_build_noalloc.restype = ctypes.c_int
     lib.kdt_trace_enable.argtypes = [ctypes.c_int32]
@@ -263,9 +278,10 @@ def kdt_build(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     levels = ctypes.c_int32(0)
-    st = lib.kdt_build(points.data_ptr(), ctypes.byref(p), ws_ptr or None, ws_bytes,
-                       outputs.perm.data_ptr(), outputs.split_vals.data_ptr(), outputs.split_dims.data_ptr(),
-                       outputs.node_offsets.data_ptr(), ctypes.byref(levels), stream.cuda_stream)
+    with torch.cuda.device(dev):  # the library works on the current device: the one holding the points
+        st = lib.kdt_build(points.data_ptr(), ctypes.byref(p), ws_ptr or None, ws_bytes,
+                           outputs.perm.data_ptr(), outputs.split_vals.data_ptr(), outputs.split_dims.data_ptr(),
+                           outputs.node_offsets.data_ptr(), ctypes.byref(levels), stream.cuda_stream)
     if st:
         raise KdtError(st, "kdt_build")
     L = levels.value
@@ -326,10 +342,11 @@ def kdt_build_noalloc(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, 
     if stream is None:
         stream = torch.cuda.current_stream(points.device)
     levels = ctypes.c_int32(0)
-    st = load_library().kdt_build_noalloc(points.data_ptr(), ctypes.byref(p), outputs.perm.data_ptr(),
-                                          outputs.split_vals.data_ptr(), outputs.split_dims.data_ptr(),
-                                          outputs.node_offsets.data_ptr(), ctypes.byref(levels),
-                                          stream.cuda_stream)
+    with torch.cuda.device(points.device):  # the scratch array used is the current device's
+        st = load_library().kdt_build_noalloc(points.data_ptr(), ctypes.byref(p), outputs.perm.data_ptr(),
+                                              outputs.split_vals.data_ptr(), outputs.split_dims.data_ptr(),
+                                              outputs.node_offsets.data_ptr(), ctypes.byref(levels),
+                                              stream.cuda_stream)
     if st:
         raise KdtError(st, "kdt_build_noalloc")
     L = levels.value
@@ -509,6 +526,17 @@ class Server:
             tree = Tree(o.perm[:n], o.split_vals[:m], o.split_dims[:m], o.node_offsets[:(1 << L) + 1], L)
         return res.value, tree, lat.value
 
+    def cancel(self, ticket: int) -> bool:
+        """Cancel a queued request (kdt_server_cancel). True if it was
+        cancelled (poll then reports KDT_ERR_CANCELLED); False if it is
+        already on the GPU or finished."""
+        st = self._lib.kdt_server_cancel(self._h, ticket)
+        if st == 8:
+            return False
+        if st:
+            raise KdtError(st, "kdt_server_cancel")
+        return True
+
     def stats(self) -> dict:
         info = kdt_server_info()
         st = self._lib.kdt_server_stats(self._h, ctypes.byref(info))
@@ -526,3 +554,16 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def fault_inject(kind: int, count: int) -> None:
+    """Fail the next `count` events of this kind on purpose (kdt_fault_inject;
+    host-side only: nothing faults the GPU)."""
+    st = load_library().kdt_fault_inject(kind, count)
+    if st:
+        raise KdtError(st, "kdt_fault_inject")
+
+
+def fault_clear() -> None:
+    """Turn every injected fault off (kdt_fault_clear)."""
+    load_library().kdt_fault_clear()

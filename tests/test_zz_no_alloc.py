@@ -1,8 +1,8 @@
 """GPU test of kdt_build_noalloc, the entry point for callers that cannot
 allocate device memory (it uses the library's fixed 64 MiB device scratch
 array as its workspace). Its results must equal kdt_build's on the same
-inputs, on two calls in a row (the second call runs over the first call's
-leftovers in the shared scratch array). Collected last on purpose."""
+inputs, on two calls in a row, and after a larger problem has left its
+tables in the shared scratch array. Collected last on purpose."""
 from __future__ import annotations
 
 import numpy as np
@@ -59,6 +59,32 @@ def test_noalloc_matches_kdt_build_twice(case):
         torch.cuda.synchronize()
         assert got[4] == ref[4]
         for a, b in zip(got[:4], ref[:4]):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_noalloc_over_a_larger_problems_leftovers():
+    """A larger widest-spread build fills more of the shared scratch array
+    with its tables; a smaller leaf-mode build that follows runs over those
+    leftovers and must still give kdt_build's bits (a counter that the build
+    failed to clear would show here)."""
+    from paper_2201_08288_gb300 import kdt
+    dev = torch.device("cuda:0")
+    big = workloads.student_t_snapped(400000, 6, 3.0, 0.1, 256, seed=21)
+    big_sid = workloads.explicit_sids(400000, 200, seed=22)
+    P = torch.from_numpy(big).to(dev)
+    S = torch.from_numpy(big_sid).to(dev)
+    kw_big = dict(r=200, subset_mode=2, depth=12, key_rule=1)
+    got_big = _host(kdt.kdt_build_noalloc(P, sid=S, outputs=_outputs(P.shape[1], 12, dev), **kw_big))
+    ref_big = _host(kdt.kdt_build(P, sid=S, outputs=_outputs(P.shape[1], 12, dev), **kw_big))
+    small = workloads.gaussian_mixture(30000, 3, 8, 0.05, seed=23)
+    Q = torch.from_numpy(small).to(dev)
+    kw_small = dict(r=16, subset_mode=0, depth=0, leaf_size=32, max_levels=16, key_rule=0)
+    got = _host(kdt.kdt_build_noalloc(Q, outputs=_outputs(Q.shape[1], 16, dev), **kw_small))
+    ref = _host(kdt.kdt_build(Q, outputs=_outputs(Q.shape[1], 16, dev), **kw_small))
+    torch.cuda.synchronize()
+    for g, r in ((got_big, ref_big), (got, ref)):
+        assert g[4] == r[4]
+        for a, b in zip(g[:4], r[:4]):
             np.testing.assert_array_equal(a, b)
 
 
