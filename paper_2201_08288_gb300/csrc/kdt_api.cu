@@ -103,7 +103,7 @@ kdt_status kdt_build(const float* points, const kdt_params* p, void* workspace, 
   cudaStream_t st = (cudaStream_t)stream;
   void* owned = nullptr;
   if (!workspace) {
-    if (cudaMalloc(&owned, pp.total) != cudaSuccess) {
+    if (kdt::dev_malloc(&owned, pp.total) != cudaSuccess) {
       (void)cudaGetLastError();
       return KDT_ERR_OOM;
     }
@@ -148,7 +148,7 @@ kdt_status kdt_build_host(const float* points_host, const kdt_params* p, void* w
   cudaStream_t st = (cudaStream_t)stream;
   void* owned = nullptr;
   if (!workspace) {
-    if (cudaMalloc(&owned, need) != cudaSuccess) {
+    if (kdt::dev_malloc(&owned, need) != cudaSuccess) {
       (void)cudaGetLastError();
       return KDT_ERR_OOM;
     }
@@ -234,6 +234,7 @@ const char* kdt_status_str(kdt_status s) {
     case KDT_ERR_LEVEL_CAP: return "leaf mode needs more than max_levels levels";
     case KDT_ERR_BUSY: return "server busy";
     case KDT_ERR_NOT_FOUND: return "unknown ticket";
+    case KDT_ERR_CANCELLED: return "request cancelled";
   }
   return "unknown status";
 }

@@ -74,7 +74,7 @@ kdt_status kdt_build_batched(const kdt_tree_desc* trees, int32_t num_trees, void
   cudaStream_t st = (cudaStream_t)stream;
   void* owned = nullptr;
   if (!workspace) {
-    if (cudaMalloc(&owned, bp.total) != cudaSuccess) {
+    if (kdt::dev_malloc(&owned, bp.total) != cudaSuccess) {
       (void)cudaGetLastError();
       return KDT_ERR_OOM;
     }

@@ -1,5 +1,6 @@
 // kdt_launch.h -- host-side declarations shared by the CUDA translation units.
 #pragma once
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
@@ -29,6 +30,7 @@ constexpr int kSubtreeCtasPerSm = 2;
 constexpr size_t kSubtreeSmemBytes = 112 * 1024;  // dynamic part, per CTA
 constexpr int kSubtreeBigCap = 1024;              // segments above the rank-counting size
 constexpr int kSubtreeSmemCells = 256;
+constexpr int kSubtreeMaxPoints = 2048;           // a cell the kernel takes: at most 8 points per thread
 constexpr size_t kSubtreeFixedBytes = (size_t)kSubtreeWarps * 256 * 4 /* warp histograms */ +
                                       (size_t)kSubtreeBigCap * 2 + 2 * (size_t)kSubtreeSmemCells * sizeof(LCell);
 
@@ -55,7 +57,7 @@ inline int subtree_capacity(int d) {
     const int mid = (lo + hi + 1) / 2;
     if (kSubtreeFixedBytes + subtree_point_bytes(mid, d) <= kSubtreeSmemBytes) lo = mid; else hi = mid - 1;
   }
-  return lo & ~31;
+  return std::min(lo & ~31, kSubtreeMaxPoints);
 }
 
 // The tuning of the select paths (kdt_tuning, validated) in force when a level
@@ -118,6 +120,13 @@ cudaError_t leaf_sort_huge(const TreeHost& th, const std::vector<TermRec>& recs,
 #include "kdt.h"
 
 namespace kdt {
+
+// Fault injection (kdt_fault.cu): true if an injected failure of this kind
+// (a kdt_fault value) is due now; it is then consumed.
+bool fault_take(int kind);
+// The library's device allocations go through here (an injected
+// KDT_FAULT_ALLOC fails it without calling cudaMalloc).
+cudaError_t dev_malloc(void** p, size_t bytes);
 
 kdt_status build_in_workspace(const float* points, const kdt_params* p, void* workspace, size_t workspace_bytes,
                               uint32_t* out_perm, float* out_split_vals, int8_t* out_split_dims,

@@ -72,11 +72,16 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t phase
   return done != 0;
 }
 
-// Bounded wait on an mbarrier phase: false if it did not complete in time.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
+// Bounded wait on an mbarrier phase: false if it did not complete within
+// `tries` suspending tries.
+__device__ __forceinline__ bool mbar_wait_bounded_n(uint64_t* bar, uint32_t phase, uint32_t tries) {
+  for (uint32_t it = 0; it < tries; ++it)
     if (mbar_try_wait_hint(bar, phase, kWaitHintNs)) return true;
   return false;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+  return mbar_wait_bounded_n(bar, phase, kSpinLimit);
 }
 
 // Bulk copy global -> shared, completion counted on `bar` (16-byte aligned

@@ -166,17 +166,38 @@ struct kdt_server {
           continue;
         }
       }
-      kdt_status s = engine->tick();
+      kdt_status s = kdt::fault_take(KDT_FAULT_SERVER_STEP) ? KDT_ERR_CUDA : engine->tick();
       if (s == KDT_OK) s = engine->done_slots(running, &done);
       if (s == KDT_OK && !done.empty()) s = engine->finalize(done, &st, &lv);
+      bool recovered = true;
+      if (s != KDT_OK) {
+        // The engine's tables no longer describe the trees in flight: clear
+        // them (after whatever the failed step left on the stream) so that
+        // queued requests can start from scratch.
+        recovered = !kdt::fault_take(KDT_FAULT_SERVER_RESET) && engine->reset() == KDT_OK &&
+                    cudaStreamSynchronize(stream) == cudaSuccess;
+        if (!recovered) (void)cudaGetLastError();
+      }
       std::lock_guard<std::mutex> lk(mu);
       info.ticks += 1;
       if (s != KDT_OK) {
-        // an engine failure ends every request in flight with that status
-        fatal = s;
+        // an engine failure ends every request in flight with that status;
+        // if the engine could not be cleared, the queued ones too
+        info.engine_failures += 1;
         done = running;
         st.assign(done.size(), s);
         lv.assign(done.size(), 0);
+        if (!recovered) {
+          fatal = s;
+          for (Request* r : queue) {
+            r->status = s;
+            r->t_done = now_ms();
+            r->state = 2;
+            info.completed += 1;
+          }
+          queue.clear();
+          cv_done.notify_all();
+        }
       }
       for (size_t i = 0; i < done.size(); ++i) {
         Request* r = slot_req[done[i]];
@@ -225,7 +246,7 @@ kdt_status kdt_server_create(size_t mem_budget_bytes, int32_t max_trees_in_fligh
     delete sv;
     return KDT_ERR_CAPACITY;
   }
-  if (cudaMalloc(&sv->mem, mem_budget_bytes) != cudaSuccess) {
+  if (kdt::dev_malloc((void**)&sv->mem, mem_budget_bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     delete sv;
     return KDT_ERR_OOM;
@@ -311,6 +332,27 @@ kdt_status kdt_server_poll(kdt_server* sv, uint64_t ticket, int32_t wait_ms, kdt
   if (latency_ms) *latency_ms = r->t_done - r->t_submit;
   sv->requests.erase(it);
   delete r;
+  return KDT_OK;
+}
+
+kdt_status kdt_server_cancel(kdt_server* sv, uint64_t ticket) {
+  if (!sv) return KDT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->requests.find(ticket);
+  if (it == sv->requests.end()) return KDT_ERR_NOT_FOUND;
+  Request* r = it->second;
+  if (r->state != 0) return KDT_ERR_BUSY;  // admitted or finished: poll it
+  for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q)
+    if (*q == r) {
+      sv->queue.erase(q);
+      break;
+    }
+  r->status = KDT_ERR_CANCELLED;
+  r->t_done = now_ms();
+  r->state = 2;
+  sv->info.cancelled += 1;
+  sv->info.completed += 1;
+  sv->cv_done.notify_all();
   return KDT_OK;
 }
 

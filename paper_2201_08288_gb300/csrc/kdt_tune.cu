@@ -82,7 +82,7 @@ kdt_status kdt_autotune(const kdt_tree_desc* trees, int32_t num_trees, void* wor
   if (s != KDT_OK) return s;
   void* owned = nullptr;
   if (!workspace) {
-    if (cudaMalloc(&owned, need) != cudaSuccess) {
+    if (kdt::dev_malloc(&owned, need) != cudaSuccess) {
       (void)cudaGetLastError();
       return KDT_ERR_OOM;
     }

@@ -137,3 +137,30 @@ def test_batched_builds_refuse_the_estimator(lib):
     assert e.value.status == 1
     descs[1].params = kdt.make_params(5000, 3, depth=6)
     assert kdt.kdt_workspace_size_batched(descs) > 0
+
+
+def test_fault_injection_is_host_state(lib):
+    """kdt_fault_inject validates its arguments on the host; kdt_fault_clear
+    turns every kind off (nothing here touches a device)."""
+    from paper_2201_08288_gb300 import kdt
+    for kind in (kdt.KDT_FAULT_ALLOC, kdt.KDT_FAULT_SERVER_STEP, kdt.KDT_FAULT_SERVER_RESET, kdt.KDT_FAULT_WAIT):
+        assert lib.kdt_fault_inject(kind, 0) == 0
+    assert lib.kdt_fault_inject(0, 1) == 1
+    assert lib.kdt_fault_inject(99, 1) == 1
+    assert lib.kdt_fault_inject(kdt.KDT_FAULT_ALLOC, -1) == 1
+    kdt.fault_inject(kdt.KDT_FAULT_ALLOC, 3)
+    kdt.fault_clear()
+    assert kdt.kdt_status_str(kdt.KDT_ERR_CANCELLED) == "request cancelled"
+
+
+def test_server_info_struct_layout_matches_header():
+    from paper_2201_08288_gb300 import kdt
+    src = open(os.path.join(ROOT, "include", "kdt.h")).read()
+    body = re.search(r"typedef struct kdt_server_info \{(.*?)\} kdt_server_info;", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            fields += [f.strip() for f in decl.split(None, 1)[1].split(",")]
+    assert fields == [f[0] for f in kdt.kdt_server_info._fields_]
