@@ -38,6 +38,8 @@ constexpr int T = kSubtreeThreads;
 constexpr int NW = kSubtreeWarps;
 constexpr uint16_t kNoCell = 0xffff;
 constexpr uint32_t kRankMax = 32;
+constexpr int kQ = kSubtreeMaxPoints / T;  // positions per thread
+static_assert(kQ * NW == 64, "the block counts of a level fill two words per lane");
 
 // -------------------------------------------------------- shared layout
 
@@ -57,31 +59,40 @@ struct Smem {
   uint16_t* aux;      // N: segment-start flag, then left flag
 };
 
-__device__ __forceinline__ uint8_t* al16(uint8_t* p) {
-  return (uint8_t*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-}
+__device__ __forceinline__ uint32_t al16(uint32_t off) { return (off + 15u) & ~15u; }
 
-__device__ Smem carve(uint8_t* base, uint32_t N, int d) {
+// Carve the dynamic shared memory with plain byte offsets from its base (no
+// pointer is stored through another pointer), so that the compiler keeps
+// every array in the shared address space.
+__device__ __forceinline__ Smem carve(uint8_t* base, uint32_t N, int d) {
   Smem s;
-  uint8_t* p = base;
-  s.whist = (uint32_t*)p;
-  p += (size_t)NW * 256 * 4;
-  s.biglist = (uint16_t*)p;
-  p += kSubtreeBigCap * 2;
-  s.tab = (LCell*)p;
-  p += 2 * kSubtreeSmemCells * sizeof(LCell);
-  const uint32_t stride = subtree_stride(N);
-  s.cols = (uint32_t*)p;
-  p += (size_t)(d + 1) * stride * 4;
-  s.gk = (uint32_t*)p;
-  p = al16(p + (size_t)N * 4);
-  s.smed = (uint32_t*)p;
-  p = al16(p + (size_t)N * 4);
-  uint16_t** arr[7] = {&s.sid, &s.ordA, &s.ordB, &s.cellid, &s.pre, &s.segs, &s.aux};
-  for (int i = 0; i < 7; ++i) {
-    *arr[i] = (uint16_t*)p;
-    p = al16(p + ((size_t)N + 1) * 2);
-  }
+  uint32_t off = 0;
+  s.whist = (uint32_t*)(base + off);
+  off += (uint32_t)NW * 256u * 4u;
+  s.biglist = (uint16_t*)(base + off);
+  off += (uint32_t)kSubtreeBigCap * 2u;
+  s.tab = (LCell*)(base + off);
+  off += 2u * (uint32_t)kSubtreeSmemCells * (uint32_t)sizeof(LCell);
+  s.cols = (uint32_t*)(base + off);
+  off += (uint32_t)(d + 1) * subtree_stride(N) * 4u;
+  s.gk = (uint32_t*)(base + off);
+  off = al16(off + N * 4u);
+  s.smed = (uint32_t*)(base + off);
+  off = al16(off + N * 4u);
+  const uint32_t a = (N + 1u) * 2u;
+  s.sid = (uint16_t*)(base + off);
+  off = al16(off + a);
+  s.ordA = (uint16_t*)(base + off);
+  off = al16(off + a);
+  s.ordB = (uint16_t*)(base + off);
+  off = al16(off + a);
+  s.cellid = (uint16_t*)(base + off);
+  off = al16(off + a);
+  s.pre = (uint16_t*)(base + off);
+  off = al16(off + a);
+  s.segs = (uint16_t*)(base + off);
+  off = al16(off + a);
+  s.aux = (uint16_t*)(base + off);
   return s;
 }
 
@@ -113,35 +124,94 @@ __device__ __forceinline__ int warp_pick_widest(const uint32_t (&lo)[2], const u
   return (int)__reduce_min_sync(0xffffffffu, (rh == mh && rl == ml) ? ib : 0xffffffffu);
 }
 
-// Block-wide exclusive scan of the flags f[0..N) into pre[0..N], pre[N] the
-// total; each thread scans a run of consecutive positions.
-__device__ __forceinline__ void scan_flags(const uint16_t* f, uint16_t* pre, uint32_t N, uint32_t* tmp) {
-  const uint32_t per = (N + T - 1) / T;
-  const uint32_t i0 = min(N, threadIdx.x * per), i1 = min(N, i0 + per);
-  uint32_t sum = 0;
-  for (uint32_t i = i0; i < i1; ++i) sum += f[i];
-  uint32_t tot;
-  uint32_t run = block_excl_scan(sum, tmp, &tot);
-  for (uint32_t i = i0; i < i1; ++i) {
-    pre[i] = (uint16_t)run;
-    run += f[i];
+// Exclusive prefix, over all positions, of the flags whose warp ballots are
+// bal[q] (position tid + q T, block q NW + warp), given the popcount of every
+// block in cnt[64] (block order = position order); *total is the sum.
+__device__ __forceinline__ void block_counts_scan(const unsigned (&bal)[kQ], const uint32_t* cnt, int lane,
+                                                  int warp, uint32_t (&excl)[kQ], uint32_t* total) {
+  const uint32_t c0 = cnt[lane], c1 = cnt[lane + 32];
+  const uint32_t i0 = warp_incl_scan(c0);
+  const uint32_t i1 = warp_incl_scan(c1) + __shfl_sync(0xffffffffu, i0, 31);
+  *total = __shfl_sync(0xffffffffu, i1, 31);
+  const uint32_t e0 = i0 - c0, e1 = i1 - c1;
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int src = (q * NW + warp) & 31;
+    const uint32_t v0 = __shfl_sync(0xffffffffu, e0, src), v1 = __shfl_sync(0xffffffffu, e1, src);
+    excl[q] = (q * NW < 32 ? v0 : v1) + (uint32_t)__popc(bal[q] & lt);
   }
-  if (threadIdx.x == 0) pre[N] = (uint16_t)tot;
+}
+
+// Block-wide exclusive scan of one value per thread with one barrier; wtot
+// (NW words) must not be reused before the next barrier.
+__device__ __forceinline__ uint32_t block_excl_scan_1bar(uint32_t v, uint32_t* wtot, int lane, int warp,
+                                                         uint32_t* total) {
+  const uint32_t incl = warp_incl_scan(v);
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const uint32_t x = wtot[w];
+    all += x;
+    before += w < warp ? x : 0u;
+  }
+  *total = all;
+  return before + incl - v;
+}
+
+// Weighted select by one warp with the items in registers (K per lane, cnt <=
+// 32 K): the smallest key m whose items with key <= m weigh more than
+// `rank`. Starting below the bits where every key agrees, each step counts
+// the weight of the remaining candidates whose next bit is 0 (one warp sum)
+// and fixes that bit.
+template <int K, class KeyOf, class WOf>
+__device__ __forceinline__ uint32_t warp_wsel_bits(uint32_t cnt, uint32_t rank, KeyOf key_of, WOf w_of) {
+  const int lane = threadIdx.x & 31;
+  uint32_t key[K], w[K];
+  uint32_t lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const uint32_t j = (uint32_t)lane + 32u * q;
+    const bool ok = j < cnt;
+    key[q] = ok ? key_of(j) : 0u;
+    w[q] = ok ? w_of(j) : 0u;
+    if (ok) {
+      lo = min(lo, key[q]);
+      hi = max(hi, key[q]);
+    }
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if (lo >= hi) return lo;
+  int bit = 31 - __clz(lo ^ hi);                    // highest bit where the keys differ
+  uint32_t prefix = lo & ~((2u << bit) - 1u);       // the bits above it (none when bit = 31)
+  for (; bit >= 0; --bit) {
+    const uint32_t fixed = ~((1u << bit) - 1u);     // bits above `bit`, and `bit` itself
+    uint32_t acc = 0;
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc += ((key[q] ^ prefix) & fixed) == 0u ? w[q] : 0u;
+    acc = __reduce_add_sync(0xffffffffu, acc);
+    if (rank >= acc) {
+      rank -= acc;
+      prefix |= 1u << bit;
+    }
+  }
+  return prefix;
 }
 
 __global__ void __launch_bounds__(T, kSubtreeCtasPerSm)
 k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t* count_dev, uint32_t* head,
-          LCell* slices, uint32_t slice_cells) {
+          LCell* slices, uint32_t slice_cells, uint32_t probe_tries) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   if (count_dev) count = min(*count_dev, count);  // a graph-driven step: the queue's length, capped
   __shared__ uint32_t tmp[33];
   __shared__ uint32_t s_item, s_ncur, s_nbig, s_where, s_fail;
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_colbase[kMaxDims + 1];
-  struct CombineState {
-    uint32_t lo, hi, rem, prefix, rank;
-  };
-  __shared__ CombineState s_cmb[kSubtreeWarps];
+  __shared__ uint32_t s_bcnt[kQ * NW];  // per-block counts of a level's position flags
+  __shared__ uint32_t s_wtot[NW];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // this CTA's two global cell tables (for levels with too many cells for
   // shared memory); tables are picked by offset, never by an indexed array,
@@ -163,6 +233,28 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
     if (item >= count) break;
     const Cell c = list[item];
     const TreeDev& t = trees[c.tree];
+    if (probe_tries && tid == 0) {
+      // injected fault (kdt_fault_inject): wait on a phase that nothing
+      // completes, with no copy in flight, until the bound gives up; each CTA
+      // probes once
+      const uint32_t tries = probe_tries;
+      probe_tries = 0;
+      if (!mbar_wait_bounded_n(&s_bar, phase, tries)) {
+        set_status(t, ST_TIMEOUT);
+        s_fail = 1;
+      }
+    }
+    __syncthreads();
+    if (s_fail) {
+      // a bounded wait of this CTA gave up: the cells it still pulls fail
+      // without being touched, so that every tree's count of cells left
+      // reaches zero and its caller gets the status
+      if (tid == 0) {
+        set_status(t, ST_TIMEOUT);
+        atomicSub(t.live, 1);
+      }
+      continue;
+    }
     const uint32_t N = c.count;
     const int d = t.d, r = t.r;
     const int64_t n = t.n;
@@ -217,29 +309,61 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
       if (!P)
         for (uint32_t i = tid; i < N; i += T) pm0[i] = b0 + i;
       // explicit subset ids are read from global memory while the bulk copies
-      // run (neither touches the other's shared memory)
+      // run (neither touches the other's shared memory), eight loads in
+      // flight per thread
       const void* SID = src_sid(t, c.level);
       const bool expl = t.subset_mode == SUB_EXPLICIT;
-      for (uint32_t i = tid; i < N; i += T) {
-        if (expl) S.sid[i] = (uint16_t)subset_of(t, SID, 0u, (int64_t)b0 + i);
-        S.cellid[i] = 0;
+      for (uint32_t i0 = tid; i0 < N; i0 += 8 * T) {
+        uint32_t v[8];
+        if (expl) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const uint32_t i = i0 + (uint32_t)q * T;
+            v[q] = i >= N ? 0u
+                          : (t.sid_bytes == 1 ? (uint32_t)((const uint8_t*)SID)[(int64_t)b0 + i]
+                                              : (uint32_t)((const uint16_t*)SID)[(int64_t)b0 + i]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const uint32_t i = i0 + (uint32_t)q * T;
+          if (i >= N) break;
+          if (expl) {
+            if (v[q] >= (uint32_t)r) {  // an id outside [0, r): reported, replaced by 0
+              set_status(t, ST_INVALID_ARG);
+              v[q] = 0;
+            }
+            S.sid[i] = (uint16_t)v[q];
+          }
+          S.cellid[i] = 0;
+        }
       }
-      if (!mbar_wait_bounded(&s_bar, phase)) {
+      // one thread waits for the copies (a waiting thread keeps issuing
+      // try_wait); the barrier after it parks the others without issue slots
+      // and makes what the copies wrote visible to them
+      if (tid == 0 && !mbar_wait_bounded(&s_bar, phase)) {
         set_status(t, ST_TIMEOUT);
-        atomicExch(&s_fail, 1u);
+        s_fail = 1;
       }
       phase ^= 1u;
       __syncthreads();
-      if (s_fail) {  // copies in flight: wait once more (bounded), then stop this CTA
-        mbar_wait_bounded(&s_bar, phase ^ 1u);
-        break;
+      if (s_fail) {  // copies in flight: wait once more (bounded), then fail this cell and drain
+        if (tid == 0) {
+          mbar_wait_bounded(&s_bar, phase ^ 1u);
+          atomicSub(t.live, 1);
+        }
+        continue;
       }
+      // keys in place; NaN is looked for in the roots of small trees only (the
+      // multi-CTA pipeline checked every point of a larger tree at its root)
       bool nan = false;
+      const bool check_nan = c.level == 0;
       for (int l = 0; l < d; ++l) {
         uint32_t* col = S.cols + s_colbase[l];
+#pragma unroll 4
         for (uint32_t i = tid; i < N; i += T) {
           const float x = __uint_as_float(col[i]);
-          nan |= is_nan_bits(x);
+          nan |= check_nan && is_nan_bits(x);
           col[i] = ord_key(x);
         }
       }
@@ -379,32 +503,63 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
         }
         __syncthreads();
 
-        // ---- 2. keys in local order, segment starts, their numbering
-        for (uint32_t i = tid; i < N; i += T) {
-          const uint16_t k = S.cellid[i];
-          uint16_t f = 0;
-          if (k != kNoCell) {
-            const uint32_t o = ordA[i];
-            S.gk[i] = S.cols[s_colbase[cc[k].dim] + o];
-            f = (i == cc[k].begin) || S.sid[o] != S.sid[ordA[i - 1]];
+        // ---- 2. keys in local order, segment starts, their numbering.
+        // Thread tid owns positions i = tid + q T (q < kQ); the 32 positions of
+        // (q, warp) form block q NW + warp, and blocks are in position order,
+        // so one scan over the kQ NW block counts of the start flags (warp
+        // ballots) numbers every segment.
+        uint32_t kq[kQ], keyq[kQ], segq[kQ];
+        unsigned balq[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          const uint32_t i = (uint32_t)tid + (uint32_t)q * T;
+          uint32_t k = kNoCell, key = 0u;
+          bool f = false;
+          if (i < N) {
+            k = S.cellid[i];
+            if (k != kNoCell) {
+              const uint32_t o = ordA[i];
+              const uint32_t cb = cc[k].begin;
+              key = S.cols[s_colbase[cc[k].dim] + o];
+              f = (i == cb) || S.sid[o] != S.sid[ordA[i - 1]];
+              S.gk[i] = key;
+            }
           }
-          S.aux[i] = f;
+          kq[q] = k;
+          keyq[q] = key;
+          balq[q] = __ballot_sync(0xffffffffu, f);
+          if (lane == 0) s_bcnt[q * NW + warp] = (uint32_t)__popc(balq[q]);
         }
         if (tid == 0) s_nbig = 0;
         __syncthreads();
-        scan_flags(S.aux, S.pre, N, tmp);
-        __syncthreads();
-        const uint32_t nseg = S.pre[N];
-        for (uint32_t i = tid; i < N; i += T)
-          if (S.aux[i]) S.segs[S.pre[i]] = (uint16_t)i;
-        if (tid == 0) S.segs[nseg] = (uint16_t)N;
+        {
+          uint32_t total;
+          block_counts_scan(balq, s_bcnt, lane, warp, segq, &total);
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            const uint32_t i = (uint32_t)tid + (uint32_t)q * T;
+            const bool f = (balq[q] >> lane) & 1u;
+            if (i < N) {
+              S.pre[i] = (uint16_t)segq[q];  // starts before position i
+              if (f) S.segs[segq[q]] = (uint16_t)i;
+            }
+            segq[q] = segq[q] + (f ? 1u : 0u) - 1u;  // the segment of position i
+          }
+          if (tid == 0) {
+            S.segs[total] = (uint16_t)N;
+            S.pre[N] = (uint16_t)total;
+          }
+        }
         __syncthreads();
 
-        // ---- 3. lower median of every segment
-        for (uint32_t i = tid; i < N; i += T) {
-          const uint16_t k = S.cellid[i];
-          if (k == kNoCell) continue;
-          const uint32_t sx = (uint32_t)S.pre[i] + S.aux[i] - 1u;
+        // ---- 3. lower median of every segment: rank counting inside the
+        // segment, or (more than kRankMax points) a warp radix select
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          const uint32_t i = (uint32_t)tid + (uint32_t)q * T;
+          const uint32_t k = kq[q];
+          if (i >= N || k == kNoCell) continue;
+          const uint32_t sx = segq[q];
           const uint32_t b = S.segs[sx], e = min((uint32_t)S.segs[sx + 1], (uint32_t)cc[k].begin + cc[k].count);
           const uint32_t w = e - b;
           if (w > kRankMax) {
@@ -414,7 +569,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
             }
             continue;
           }
-          const uint32_t key = S.gk[i];
+          const uint32_t key = keyq[q];
           uint32_t rk = 0;
           for (uint32_t j = b; j < e; ++j) {
             const uint32_t kj = S.gk[j];
@@ -423,7 +578,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
           if (rk == (w - 1) / 2) S.smed[sx] = key;
         }
         __syncthreads();
-        {
+        if (s_nbig) {
           const uint32_t nbig = min(s_nbig, (uint32_t)kSubtreeBigCap);
           for (uint32_t j = warp; j < nbig; j += NW) {
             const uint32_t sx = S.biglist[j];
@@ -436,102 +591,33 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
                                                           [](uint32_t) { return 1u; });
             if (lane == 0) S.smed[sx] = m;
           }
+          __syncthreads();
         }
-        __syncthreads();
 
         // ---- 4. weighted lower median per cell: the smallest segment median m
         // whose segments with median <= m hold >= ceil(W/2) points, i.e. the
-        // key of weighted rank (W-1)/2. A cell's segments are [pre[begin], pre[end]).
-        if (ncur >= (uint32_t)NW) {  // many cells: a warp per cell
-          for (uint32_t k = warp; k < ncur; k += NW) {
-            const uint32_t b = cc[k].begin, e = b + cc[k].count;
-            const uint32_t s0 = S.pre[b], s1 = S.pre[e];
-            const uint32_t m = warp_weighted_select(
-                s1 - s0, (cc[k].count - 1u) / 2u, S.whist + warp * 256, [&](uint32_t j) { return S.smed[s0 + j]; },
-                [&](uint32_t j) { return min((uint32_t)S.segs[s0 + j + 1], e) - S.segs[s0 + j]; });
-            if (lane == 0) cc[k].mkey = m;
-          }
-        } else {
-          // few cells: G warps per cell add into the cell's one 256-bin
-          // histogram; warp k finds cell k's digit and zeroes the bins it read.
-          // Every cell starts at the first bit where its segment medians differ.
-          const uint32_t G = (uint32_t)NW / ncur;
-          const uint32_t k = warp / G, part = warp % G;
-          uint32_t e = 0, s0 = 0, s1 = 0;
-          if (k < ncur) {
-            const uint32_t b = cc[k].begin;
-            e = b + cc[k].count;
-            s0 = S.pre[b];
-            s1 = S.pre[e];
-          }
-          uint32_t* hist = S.whist;  // [ncur][256], ncur < NW
-          for (uint32_t j = tid; j < ncur * 256u; j += T) hist[j] = 0;
-          if (tid < ncur) {
-            s_cmb[tid].lo = 0xffffffffu;
-            s_cmb[tid].hi = 0u;
-          }
-          __syncthreads();
-          if (k < ncur) {
-            uint32_t lo = 0xffffffffu, hi = 0u;
-            for (uint32_t j = s0 + part * 32 + lane; j < s1; j += G * 32) {
-              lo = min(lo, S.smed[j]);
-              hi = max(hi, S.smed[j]);
-            }
-            lo = __reduce_min_sync(0xffffffffu, lo);
-            hi = __reduce_max_sync(0xffffffffu, hi);
-            if (lane == 0) {
-              atomic_min_shared(&s_cmb[k].lo, lo);
-              atomic_max_shared(&s_cmb[k].hi, hi);
-            }
-          }
-          __syncthreads();
-          if (tid < ncur) {
-            const uint32_t lo = s_cmb[tid].lo, hi = s_cmb[tid].hi;
-            const int rem = lo >= hi ? 0 : 32 - __clz(lo ^ hi);
-            s_cmb[tid].rem = (uint32_t)rem;
-            s_cmb[tid].prefix = rem == 0 ? lo : (rem == 32 ? 0u : (lo & ~((1u << rem) - 1u)));
-            s_cmb[tid].rank = (cc[tid].count - 1u) / 2u;
-          }
-          __syncthreads();
-          for (;;) {
-            uint32_t more = 0;
-            for (uint32_t kk = 0; kk < ncur; ++kk) more |= s_cmb[kk].rem;
-            if (!more) break;
-            if (k < ncur) {
-              const uint32_t rem = s_cmb[k].rem, prefix = s_cmb[k].prefix;
-              if (rem > 0) {
-                const uint32_t bits = rem < 8u ? rem : 8u;
-                const uint32_t shift = rem - bits, nb = 1u << bits;
-                const uint32_t hmask = rem >= 32u ? 0u : ~((1u << rem) - 1u);
-                uint32_t* h = hist + k * 256u;
-                for (uint32_t j = s0 + part * 32 + lane; j < s1; j += G * 32) {
-                  const uint32_t key = S.smed[j];
-                  if ((key & hmask) == prefix)
-                    atomic_add_shared(&h[(key >> shift) & (nb - 1u)], min((uint32_t)S.segs[j + 1], e) - S.segs[j]);
-                }
-              }
-            }
-            __syncthreads();
-            if ((uint32_t)warp < ncur) {
-              const uint32_t rem = s_cmb[warp].rem;
-              if (rem > 0) {
-                const uint32_t bits = rem < 8u ? rem : 8u;
-                const uint32_t shift = rem - bits, nb = 1u << bits;
-                uint32_t* h = hist + warp * 256u;
-                uint32_t below;
-                const uint32_t digit = warp_find_digit_n(h, nb, s_cmb[warp].rank, &below);
-                __syncwarp();  // every lane has read its bins
-                for (uint32_t i = lane; i < nb; i += 32) h[i] = 0;  // ready for the next pass
-                if (lane == 0) {
-                  s_cmb[warp].rank -= below;
-                  s_cmb[warp].prefix |= digit << shift;
-                  s_cmb[warp].rem = shift;
-                }
-              }
-            }
-            __syncthreads();
-          }
-          if (tid < ncur) cc[tid].mkey = s_cmb[tid].prefix;
+        // key of weighted rank (W-1)/2. A cell's segments are [pre[begin],
+        // pre[end]). One warp per cell, no block barrier: up to 256 segments
+        // are held in registers and the key is settled one bit per step by a
+        // warp sum; more segments go through the warp's radix histogram.
+        for (uint32_t k = warp; k < ncur; k += NW) {
+          const uint32_t b = cc[k].begin, e = b + cc[k].count;
+          const uint32_t s0 = S.pre[b], s1 = S.pre[e], ns = s1 - s0;
+          const uint32_t rank = (cc[k].count - 1u) / 2u;
+          auto key_of = [&](uint32_t j) { return S.smed[s0 + j]; };
+          auto w_of = [&](uint32_t j) { return min((uint32_t)S.segs[s0 + j + 1], e) - S.segs[s0 + j]; };
+          uint32_t m;
+          if (ns <= 32u)
+            m = warp_wsel_bits<1>(ns, rank, key_of, w_of);
+          else if (ns <= 64u)
+            m = warp_wsel_bits<2>(ns, rank, key_of, w_of);
+          else if (ns <= 128u)
+            m = warp_wsel_bits<4>(ns, rank, key_of, w_of);
+          else if (ns <= 256u)
+            m = warp_wsel_bits<8>(ns, rank, key_of, w_of);
+          else
+            m = warp_weighted_select(ns, rank, S.whist + warp * 256, key_of, w_of);
+          if (lane == 0) cc[k].mkey = m;
         }
         __syncthreads();
         for (uint32_t k = tid; k < ncur; k += T) {
@@ -539,40 +625,47 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
           t.out_dims[cc[k].heap] = (int8_t)cc[k].dim;
         }
 
-        // ---- 5. stable partition of the local order (key <= split to the left);
-        // the left flags are formed inside the scan
+        // ---- 5. stable partition of the local order (key <= split to the
+        // left): left ranks from warp ballots and one scan of the block counts
         {
-          const uint32_t per = (N + T - 1) / T;
-          const uint32_t q0 = min(N, tid * per), q1 = min(N, q0 + per);
-          uint32_t sum = 0;
-          for (uint32_t q = q0; q < q1; ++q) {
-            const uint16_t k = S.cellid[q];
-            const uint16_t f = (k != kNoCell) && S.gk[q] <= cc[k].mkey;
-            S.aux[q] = f;
-            sum += f;
+          unsigned lbq[kQ];
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            const uint32_t i = (uint32_t)tid + (uint32_t)q * T;
+            const uint32_t k = kq[q];
+            const bool left = i < N && k != kNoCell && keyq[q] <= cc[k].mkey;
+            lbq[q] = __ballot_sync(0xffffffffu, left);
+            if (lane == 0) s_bcnt[q * NW + warp] = (uint32_t)__popc(lbq[q]);
           }
-          uint32_t tot;
-          uint32_t run = block_excl_scan(sum, tmp, &tot);
-          for (uint32_t q = q0; q < q1; ++q) {
-            S.pre[q] = (uint16_t)run;
-            run += S.aux[q];
+          __syncthreads();
+          uint32_t lpre[kQ], tot;
+          block_counts_scan(lbq, s_bcnt, lane, warp, lpre, &tot);
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            const uint32_t i = (uint32_t)tid + (uint32_t)q * T;
+            if (i < N) S.pre[i] = (uint16_t)lpre[q];  // left points before position i
           }
           if (tid == 0) S.pre[N] = (uint16_t)tot;
-        }
-        __syncthreads();
-        for (uint32_t k = tid; k < ncur; k += T)
-          cc[k].lcount = (uint16_t)(S.pre[cc[k].begin + cc[k].count] - S.pre[cc[k].begin]);
-        for (uint32_t i = tid; i < N; i += T) {
-          const uint16_t k = S.cellid[i];
-          if (k == kNoCell) {
-            ordB[i] = ordA[i];
-            continue;
+          __syncthreads();
+          for (uint32_t k = tid; k < ncur; k += T)
+            cc[k].lcount = (uint16_t)(S.pre[cc[k].begin + cc[k].count] - S.pre[cc[k].begin]);
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            const uint32_t i = (uint32_t)tid + (uint32_t)q * T;
+            if (i >= N) continue;
+            const uint32_t k = kq[q];
+            const uint16_t o = ordA[i];
+            if (k == kNoCell) {
+              ordB[i] = o;
+              continue;
+            }
+            const uint32_t b = cc[k].begin;
+            const uint32_t pb = S.pre[b];
+            const uint32_t L = (uint32_t)S.pre[b + cc[k].count] - pb;
+            const uint32_t lb = lpre[q] - pb;
+            const uint32_t dst = ((lbq[q] >> lane) & 1u) ? b + lb : b + L + (i - b - lb);
+            ordB[dst] = o;
           }
-          const uint32_t b = cc[k].begin;
-          const uint32_t lb = (uint32_t)S.pre[i] - S.pre[b];
-          const uint32_t L = (uint32_t)S.pre[b + cc[k].count] - S.pre[b];
-          const uint32_t dst = S.aux[i] ? b + lb : b + L + (i - b - lb);
-          ordB[dst] = ordA[i];
         }
         __syncthreads();
         {
@@ -581,28 +674,15 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
           ordB = x;
         }
 
-        // ---- 6. children: one scan over the cells numbers the live children
+        // ---- 6. children: a scan over the cells numbers the live children
         // (their number is parked in the parent's mkey); then every position
         // takes its child's number
         const int nlevel = level + 1;
-        uint32_t total_live = 0;
-        {
-          // count the live children first to choose where the next table lives
-          uint32_t sum = 0;
-          for (uint32_t k = tid; k < ncur; k += T) {
-            const LCell p = cc[k];
-            const uint32_t L = p.lcount, R = p.count - L;
-            const int stall = (R == 0) ? p.stall + 1 : 0;
-            const bool cap = t.depth == 0 && nlevel >= t.max_levels;
-            sum += (!is_terminal(t, L, nlevel, stall) && !cap) + (!is_terminal(t, R, nlevel, stall) && !cap);
-          }
-          block_excl_scan(sum, tmp, &total_live);
-        }
-        const int nwhere = total_live <= (uint32_t)kSubtreeSmemCells ? 0 : 1;
-        LCell* nc = nwhere ? gslice + (size_t)(which ^ 1) * slice_cells : S.tab + (which ^ 1) * kSubtreeSmemCells;
         uint32_t run_out = 0;
-        for (uint32_t k0 = 0; k0 < ncur; k0 += T) {
-          const uint32_t k = k0 + tid;
+        int nwhere = 0;
+        if (ncur <= (uint32_t)T) {
+          // a cell per thread: one scan with a single barrier
+          const uint32_t k = tid;
           LCell ch[2] = {};
           bool live[2] = {false, false};
           if (k < ncur) {
@@ -625,25 +705,78 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
             }
           }
           const uint32_t nlive = (uint32_t)live[0] + (uint32_t)live[1];
-          uint32_t tot;
-          const uint32_t ex = block_excl_scan(nlive, tmp, &tot);
+          const uint32_t ex = block_excl_scan_1bar(nlive, s_wtot, lane, warp, &run_out);
+          nwhere = run_out <= (uint32_t)kSubtreeSmemCells ? 0 : 1;
+          LCell* nc = nwhere ? gslice + (size_t)(which ^ 1) * slice_cells : S.tab + (which ^ 1) * kSubtreeSmemCells;
           if (k < ncur) {
-            const uint32_t li = live[0] ? run_out + ex : kNoCell;
-            const uint32_t ri = live[1] ? run_out + ex + (live[0] ? 1u : 0u) : kNoCell;
+            const uint32_t li = live[0] ? ex : kNoCell;
+            const uint32_t ri = live[1] ? ex + (live[0] ? 1u : 0u) : kNoCell;
             if (live[0]) nc[li] = ch[0];
             if (live[1]) nc[ri] = ch[1];
             cc[k].mkey = li | (ri << 16);
           }
-          run_out += tot;
+        } else {
+          uint32_t total_live = 0;
+          {
+            // count the live children first to choose where the next table lives
+            uint32_t sum = 0;
+            for (uint32_t k = tid; k < ncur; k += T) {
+              const LCell p = cc[k];
+              const uint32_t L = p.lcount, R = p.count - L;
+              const int stall = (R == 0) ? p.stall + 1 : 0;
+              const bool cap = t.depth == 0 && nlevel >= t.max_levels;
+              sum += (!is_terminal(t, L, nlevel, stall) && !cap) + (!is_terminal(t, R, nlevel, stall) && !cap);
+            }
+            block_excl_scan(sum, tmp, &total_live);
+          }
+          nwhere = total_live <= (uint32_t)kSubtreeSmemCells ? 0 : 1;
+          LCell* nc = nwhere ? gslice + (size_t)(which ^ 1) * slice_cells : S.tab + (which ^ 1) * kSubtreeSmemCells;
+          for (uint32_t k0 = 0; k0 < ncur; k0 += T) {
+            const uint32_t k = k0 + tid;
+            LCell ch[2] = {};
+            bool live[2] = {false, false};
+            if (k < ncur) {
+              const LCell p = cc[k];
+              const uint32_t L = p.lcount, R = p.count - L;
+              const int stall = (R == 0) ? p.stall + 1 : 0;
+              const uint32_t cbeg[2] = {p.begin, p.begin + L};
+              const uint32_t cn[2] = {L, R};
+#pragma unroll
+              for (int side = 0; side < 2; ++side) {
+                const uint32_t heap = 2u * p.heap + 1u + (uint32_t)side;
+                if (is_terminal(t, cn[side], nlevel, stall)) {
+                  record_terminal(t, c.begin + cbeg[side], cn[side], heap, nlevel);
+                } else if (t.depth == 0 && nlevel >= t.max_levels) {
+                  set_status(t, ST_LEVEL_CAP);
+                } else {
+                  ch[side] = LCell{heap, 0u, (uint16_t)cbeg[side], (uint16_t)cn[side], 0, 0, (uint8_t)stall};
+                  live[side] = true;
+                }
+              }
+            }
+            const uint32_t nlive = (uint32_t)live[0] + (uint32_t)live[1];
+            uint32_t tot;
+            const uint32_t ex = block_excl_scan(nlive, tmp, &tot);
+            if (k < ncur) {
+              const uint32_t li = live[0] ? run_out + ex : kNoCell;
+              const uint32_t ri = live[1] ? run_out + ex + (live[0] ? 1u : 0u) : kNoCell;
+              if (live[0]) nc[li] = ch[0];
+              if (live[1]) nc[ri] = ch[1];
+              cc[k].mkey = li | (ri << 16);
+            }
+            run_out += tot;
+          }
         }
         if (tid == 0) {
           s_ncur = run_out;
           s_where = (uint32_t)nwhere;
         }
         __syncthreads();
-        for (uint32_t i = tid; i < N; i += T) {
-          const uint16_t k = S.cellid[i];
-          if (k == kNoCell) continue;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          const uint32_t i = (uint32_t)tid + (uint32_t)q * T;
+          const uint32_t k = kq[q];
+          if (i >= N || k == kNoCell) continue;
           const uint32_t side = (i - cc[k].begin) >= cc[k].lcount ? 16u : 0u;
           S.cellid[i] = (uint16_t)(cc[k].mkey >> side);
         }
@@ -744,8 +877,9 @@ void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, cons
                     cudaStream_t st) {
   if (count == 0) return;
   cudaMemsetAsync(head, 0, sizeof(uint32_t), st);
+  const uint32_t probe = fault_take(KDT_FAULT_WAIT) ? 1024u : 0u;
   TraceScope ts(K_SUBTREE, st, points);
-  k_subtree<<<grid, T, kSubtreeSmemBytes, st>>>(trees, list, count, count_dev, head, slices, slice_cells);
+  k_subtree<<<grid, T, kSubtreeSmemBytes, st>>>(trees, list, count, count_dev, head, slices, slice_cells, probe);
 }
 
 void launch_finalize_many(const TreeDev* trees, const uint32_t* slots, uint32_t nslots, uint32_t max_records,
