@@ -321,8 +321,11 @@ def run_serving(args, dev, kdt) -> dict:
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     solo_units = 0
+    solo_lat = []
     for p_, s in zip(pts_s, sample):
-        t = kdt.kdt_build(p_, workspace=ws1, stream=stream, **kw_of(s))
+        t1 = time.perf_counter()
+        t = kdt.kdt_build(p_, workspace=ws1, stream=stream, **kw_of(s))  # returns when built
+        solo_lat.append(1e3 * (time.perf_counter() - t1))
         solo_units += int(s.n) * t.levels
     torch.cuda.synchronize()
     solo_s = time.perf_counter() - t0
@@ -372,7 +375,9 @@ def run_serving(args, dev, kdt) -> dict:
             "latency_ms": {"p50": _pct(lat, 0.5), "p99": _pct(lat, 0.99), "max": max(lat)},
             "peak_in_flight": info["peak_in_flight"], "outstanding_max": backlog_max,
             "solo": {"value": solo_units / solo_s, "unit": UNIT, "requests_per_s": len(sample) / solo_s,
-                     "what": f"the first {len(sample)} requests, one kdt_build each, back to back"},
+                     "latency_ms": {"p50": _pct(solo_lat, 0.5), "p99": _pct(solo_lat, 0.99), "max": max(solo_lat)},
+                     "what": f"the first {len(sample)} requests, one kdt_build each, back to back "
+                             "(latency: each build alone, call to return)"},
             "served_vs_solo": (units / wall) / (solo_units / solo_s)}
 
 
@@ -388,6 +393,10 @@ def main() -> None:
     ap.add_argument("--load", type=float, default=0.7, help="c5: arrival rate / solo capacity")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="c3: skip the batched (config 4) and served (config 5) sub-records")
+    ap.add_argument("--extra-requests", type=int, default=3000,
+                    help="c3: requests of the served sub-record (config 5's stream, first N arrivals)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -534,6 +543,29 @@ def main() -> None:
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
 
+    extra = {}
+    if args.workload == "c3" and world == 1 and not args.no_extra:
+        # the batching and serving patterns on their own configurations, beside
+        # the plain build: all 4096 trees of config 4 against the same trees
+        # built one by one, and config 5's stream (its first N arrivals)
+        # against the same requests built one by one
+        del pts, sid, out
+        if "ws" in locals():
+            del ws
+        if e2e is not None:
+            del ws_h, host_pts, host_sid, houts
+        torch.cuda.empty_cache()
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup = 3, 3
+        b = run_batched(sub, dev, kdt)
+        extra["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "solo_loop",
+                                              "batched_vs_solo", "gpu_launches", "clocks")}
+        torch.cuda.empty_cache()
+        sub.requests = args.extra_requests
+        sv = run_serving(sub, dev, kdt)
+        extra["served"] = {k: sv[k] for k in ("value", "unit", "ms_per_step", "config", "latency_ms", "solo",
+                                              "served_vs_solo", "peak_in_flight", "outstanding_max")}
+
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -548,7 +580,7 @@ def main() -> None:
             "build_model_gbs": build_model_gbs, "build_model_frac": build_model_gbs / peak,
             "model_bytes_per_point_level": mb,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "kernels": kernel_table,
+            "kernels": kernel_table, **extra,
         }))
     if dist:
         dist.destroy_process_group()
