@@ -320,6 +320,29 @@ kdt_status kdt_build_noalloc(const float *points, const kdt_params *p, uint32_t 
                              float *out_split_vals, int8_t *out_split_dims,
                              int64_t *out_node_offsets, int32_t *out_levels, void *stream);
 
+/* ---- sharded build --------------------------------------------------------
+ * The paper's distributed setting (App. C.2: the data stays in its R subsets,
+ * a map step runs on each and a reduce combines their statistics; Sec. 3.2:
+ * statistics of any partition into subsets combine exactly), emulated with
+ * `shards` logical shards on the current device. Subset s belongs to shard
+ * s % shards; each shard holds only its own points. Every level, each shard
+ * takes the lower median and size of its (cell, subset) segments, an
+ * all-gather among the shards hands everyone the other shards' pairs of the
+ * same cell (and, for widest spread, the per-coordinate min / max of the
+ * root and of every child), every shard runs the same combine, and the
+ * partition is local. At the end the shards' leaves are merged by original
+ * index. The outputs are bit-identical to kdt_build's for the same points and
+ * parameters.
+ *   Depth mode only (p->depth >= 1; fourier_j = 0); 1 <= shards <= 16.
+ *   Arguments and outputs as kdt_build (no workspace: the call allocates its
+ *   own with cudaMalloc, in two parts, and frees it before returning).
+ * Errors: KDT_ERR_INVALID_ARG (also: depth 0, fourier_j > 0, shards out of
+ *         range, an explicit subset id >= r), KDT_ERR_NAN_INPUT, KDT_ERR_OOM,
+ *         KDT_ERR_CUDA. */
+kdt_status kdt_build_sharded(const float *points, const kdt_params *p, int32_t shards, uint32_t *out_perm,
+                             float *out_split_vals, int8_t *out_split_dims, int64_t *out_node_offsets,
+                             int32_t *out_levels, void *stream);
+
 /* ---- fault injection ----------------------------------------------------
  * Host-side hooks that make a failure happen on purpose, so that the error
  * paths can be tested without faulting a GPU. All are off by default; each

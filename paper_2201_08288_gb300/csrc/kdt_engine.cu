@@ -94,7 +94,7 @@ kdt_params effective_params(const kdt_params& p) {
   return e;
 }
 
-TreePlan plan_tree(const kdt_params& p0) {
+TreePlan plan_tree(const kdt_params& p0, bool no_subtree) {
   const kdt_params p = effective_params(p0);
   TreePlan t;
   const uint64_t n = (uint64_t)p.n;
@@ -103,7 +103,7 @@ TreePlan plan_tree(const kdt_params& p0) {
   // the estimator's splits come from the multi-CTA steps only (no subtree
   // kernel); its cells keep index order (no presort), so no leaf sort either
   const bool fourier = p.fourier_j > 0;
-  t.small_max = fourier ? 0 : subtree_capacity(p.d);
+  t.small_max = (fourier || no_subtree) ? 0 : subtree_capacity(p.d);
   t.sid_bytes = p.subset_mode == KDT_SUBSET_EXPLICIT ? (p.subset_id16 ? 2 : 1) : 0;
   const bool root_terminal = p.depth > 0 ? (n == 0) : (n <= (uint64_t)p.leaf_size);
   t.leafsort = !root_terminal && p.subset_mode != KDT_SUBSET_CONTIGUOUS && !fourier;

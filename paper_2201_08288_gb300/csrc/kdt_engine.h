@@ -40,7 +40,9 @@ struct TreePlan {
          huge = 0, words = 0;
   size_t bytes = 0;
 };
-TreePlan plan_tree(const kdt_params& p);
+// no_subtree: every cell stays in the multi-CTA pipeline (a sharded build's
+// trees, whose splits are exchanged level by level).
+TreePlan plan_tree(const kdt_params& p, bool no_subtree = false);
 
 // Capacities of the shared tables, accumulated over the trees they must serve
 // at the same time.
@@ -70,6 +72,15 @@ class Engine {
 
   // Clear every counter (call once before the first admit).
   kdt_status reset();
+  // Make the forest's trees 0..shards-1 the shards of one tree (see
+  // StepDev::shards); the tables are device memory of the caller.
+  void set_sharding(uint32_t shards, uint32_t span, uint32_t* idx, uint32_t* wcount, uint32_t* mm_tmp) {
+    s_.shards = shards;
+    s_.shard_span = span;
+    s_.shard_idx = idx;
+    s_.wcount = wcount;
+    s_.mm_tmp = mm_tmp;
+  }
   // Put a tree into `slot`. tree_base holds TreePlan::bytes of device memory.
   kdt_status admit(uint32_t slot, const float* points, const kdt_params& p, const TreePlan& tp, uint8_t* tree_base,
                    uint32_t* out_perm, float* out_vals, int8_t* out_dims, int64_t* out_offs);

@@ -165,6 +165,14 @@ struct StepDev {
   uint32_t pad4;
   uint2* crow;                // [ncells][2] (slot, row of off_next) of each big child; (kNoRow, slot in
                               // small) of a child queued for the subtree kernel; else (kNoRow, kNoRow)
+  // Sharded build (0 shards: off). The forest's trees 0..shards-1 are the
+  // shards of one tree, each owning the subsets s with s % shards == its
+  // slot, all at the same level in every step.
+  uint32_t shards;
+  uint32_t shard_span;        // 2^(levels - 1): entries per shard of shard_idx
+  uint32_t* shard_idx;        // [shards][shard_span] step cell of (shard, heap - (2^level - 1)), or kNoRow
+  uint32_t* wcount;           // [ncells] points of the cell over all shards (the combine's weight)
+  uint32_t* mm_tmp;           // [ncells][2][d][2] children's min / max over all shards
 };
 
 constexpr uint32_t kNoRow = 0xffffffffu;
@@ -244,6 +252,12 @@ __device__ __forceinline__ uint32_t subset_at(const TreeDev& t, int level, int64
 // reads (clamped to the capacity of the cell lists).
 __device__ __forceinline__ uint32_t ncells_of(const StepDev& s) {
   return s.ncells_dev ? min(*s.ncells_dev, s.next_big_cap) : s.ncells;
+}
+
+// Points of step cell c whose split is being combined: its own count, or in a
+// sharded build the cell's count over all shards.
+__device__ __forceinline__ uint32_t cell_weight(const StepDev& s, uint32_t c, const Cell& cell) {
+  return s.shards ? s.wcount[c] : cell.count;
 }
 
 __device__ __forceinline__ bool is_terminal(const TreeDev& t, uint32_t count, int level, int stall) {

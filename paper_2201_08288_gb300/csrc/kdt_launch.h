@@ -86,6 +86,12 @@ cudaError_t prepare_scatter_kernel();
 void launch_scatter(const TreeDev* trees, const StepDev& s, uint32_t max_tiles, uint32_t grid_cap,
                     uint64_t points, int uniform_d, cudaStream_t st);
 
+// Sharded build (kdt_shard.cu): the per-level exchanges among the shards of
+// a step whose StepDev has shards > 0 (ncells_cap bounds the step's cells).
+void launch_shard_index(const StepDev& s, uint32_t ncells_cap, cudaStream_t st);
+void launch_shard_medians(const TreeDev* trees, const StepDev& s, uint32_t ncells_cap, cudaStream_t st);
+void launch_shard_minmax(const TreeDev* trees, const StepDev& s, uint32_t ncells_cap, cudaStream_t st);
+
 cudaError_t prepare_subtree_kernel();
 // count_dev: if set, the device word holding the queue's length (count is
 // then its cap)

@@ -407,7 +407,9 @@ __device__ __forceinline__ void pick_dim_cell(const TreeDev* trees, const StepDe
     shi[l] = 0u;
   }
   __syncthreads();
-  const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
+  // the roots of a sharded build's shards are parts of one root: every one
+  // of them reduces the tiles of all
+  const uint32_t tb = s.shards ? 0u : s.tile_base[c], te = s.shards ? s.tile_base[ncells_of(s)] : s.tile_base[c + 1];
   const int lane = threadIdx.x & 31;
   for (int c0 = 0; c0 < t.d; c0 += 8) {
     const int nc = min(8, t.d - c0);
@@ -867,7 +869,7 @@ __device__ __forceinline__ void combine_cell(const TreeDev* trees, const StepDev
   const TreeDev& t = trees[cell.tree];
   const int r = t.r;
   const uint32_t g0 = s.seg_base[c];
-  uint32_t rank = (cell.count - 1) / 2, prefix = 0, mask = 0;
+  uint32_t rank = (cell_weight(s, c, cell) - 1) / 2, prefix = 0, mask = 0;
   for (int shift = 24; shift >= 0; shift -= 8) {
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
@@ -919,7 +921,7 @@ __device__ __forceinline__ void combine_warp_cell(const TreeDev* trees, const St
   const uint32_t* med = s.seg_med + g0;
   const uint32_t* wt = s.seg_w + g0;
   const uint32_t m = warp_weighted_select(
-      (uint32_t)t.r, (cell.count - 1) / 2, hist[warp], [&](uint32_t j) { return med[j]; },
+      (uint32_t)t.r, (cell_weight(s, c, cell) - 1) / 2, hist[warp], [&](uint32_t j) { return med[j]; },
       [&](uint32_t j) { return wt[j]; }, [&](uint32_t j) { return wt[j] != 0u; });
   if (lane == 0) {
     s.mkey[c] = m;
@@ -1380,6 +1382,7 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
   };
   { TraceScope ts(K_PREP, st); k_prep<<<1, 1024, 0, st>>>(trees, s); }
   { TraceScope ts(K_TILES, st); k_tiles<<<cells_grid(1, sms * 8u), 256, 0, st>>>(trees, s); }
+  if (s.shards) launch_shard_index(s, nc, st);
   if (has_roots) {
     {
       TraceScope ts(K_PS_COUNT, st, points);
@@ -1428,6 +1431,7 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
           k_select_big<256, 11><<<grid, 256, 0, st>>>(trees, s);
       }
     }
+    if (s.shards) launch_shard_medians(trees, s, nc, st);  // the all-gather of the segment statistics
     {
       TraceScope ts(K_COMBINE, st);
       if (many)
@@ -1449,6 +1453,7 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
   }
   { TraceScope ts(K_CLASSIFY, st); k_classify<<<cells_grid(256, sms * 4u), 256, 0, st>>>(trees, s); }
   launch_scatter(trees, s, max_tiles, 2 * sms, points, uniform_d, st);
+  if (any_widest && s.shards) launch_shard_minmax(trees, s, nc, st);
   if (any_widest) {
     TraceScope ts(K_CHILD_DIMS, st);
     k_child_dims<<<cells_grid(8, sms * 8u), 256, 0, st>>>(trees, s);

@@ -16,7 +16,8 @@ const char* const kNames[K_NUM] = {
     "k_minmax",     "k_pick_dim",   "k_select_tiny", "k_select_small", "k_select_big", "k_combine",    "k_part_count",
     "k_part_scan",  "k_classify",   "k_part_scatter", "k_child_dims",  "k_subtree",
     "k_finalize",   "k_iota",       "k_leaf_sort",  "k_leaf_hist",   "k_leaf_scan",   "k_leaf_scatter",
-    "k_leaf_copy",  "k_fourier_moments", "k_fourier_split"};
+    "k_leaf_copy",  "k_fourier_moments", "k_fourier_split", "k_shard_exchange", "k_shard_split",
+    "k_shard_merge"};
 
 struct Pending {
   KernelId id;

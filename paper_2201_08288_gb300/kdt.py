@@ -42,7 +42,7 @@ EXPORTED = ["kdt_workspace_size", "kdt_build", "kdt_workspace_size_host", "kdt_b
             "kdt_trace_read", "kdt_build_noalloc", "kdt_workspace_size_batched", "kdt_build_batched",
             "kdt_server_create", "kdt_server_submit", "kdt_server_poll", "kdt_server_stats",
             "kdt_server_destroy", "kdt_server_cancel", "kdt_tuning_default", "kdt_set_tuning", "kdt_get_tuning",
-            "kdt_autotune", "kdt_fault_inject", "kdt_fault_clear"]
+            "kdt_autotune", "kdt_fault_inject", "kdt_fault_clear", "kdt_build_sharded"]
 
 
 class KdtError(RuntimeError):
@@ -149,6 +149,8 @@ def load_library(path: str = LIB_PATH):
     lib.kdt_server_cancel.restype = ctypes.c_int
     lib.kdt_fault_inject.argtypes = [ctypes.c_int, ctypes.c_int32]
     lib.kdt_fault_inject.restype = ctypes.c_int
+    lib.kdt_build_sharded.argtypes = [vp, P, ctypes.c_int32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), vp]
+    lib.kdt_build_sharded.restype = ctypes.c_int
     lib.kdt_fault_clear.argtypes = []
     lib.kdt_fault_clear.restype = None
     lib.kdt_build_noalloc.argtypes = [vp, P, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), vp]
@@ -349,6 +351,38 @@ def kdt_build_noalloc(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, 
                                               stream.cuda_stream)
     if st:
         raise KdtError(st, "kdt_build_noalloc")
+    L = levels.value
+    m = (1 << L) - 1
+    return Tree(outputs.perm[:n], outputs.split_vals[:m], outputs.split_dims[:m],
+                outputs.node_offsets[:(1 << L) + 1], L)
+
+
+def kdt_build_sharded(points, shards: int, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None,
+                      depth: int, key_rule: int = KDT_KEY_CYCLIC, stream=None,
+                      outputs: Optional[Tree] = None) -> Tree:
+    """The build emulated on `shards` logical shards (subset s on shard
+    s % shards; per-level all-gather of the segment statistics), depth mode.
+    Same arguments and outputs as kdt_build."""
+    import torch
+    if not (points.is_cuda and points.dtype == torch.float32 and points.is_contiguous() and points.dim() == 2):
+        raise ValueError("points must be a contiguous float32 CUDA tensor [d, n]")
+    d, n = points.shape
+    sid_ptr, sid_bytes = _sid_info(sid)
+    p = make_params(n, d, r=r, subset_mode=subset_mode, sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth,
+                    key_rule=key_rule)
+    dev = points.device
+    if outputs is None:
+        outputs = _alloc_outputs(n, depth, dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    levels = ctypes.c_int32(0)
+    with torch.cuda.device(dev):
+        st = load_library().kdt_build_sharded(points.data_ptr(), ctypes.byref(p), shards, outputs.perm.data_ptr(),
+                                              outputs.split_vals.data_ptr(), outputs.split_dims.data_ptr(),
+                                              outputs.node_offsets.data_ptr(), ctypes.byref(levels),
+                                              stream.cuda_stream)
+    if st:
+        raise KdtError(st, "kdt_build_sharded")
     L = levels.value
     m = (1 << L) - 1
     return Tree(outputs.perm[:n], outputs.split_vals[:m], outputs.split_dims[:m],

@@ -164,3 +164,16 @@ def test_server_info_struct_layout_matches_header():
         if decl:
             fields += [f.strip() for f in decl.split(None, 1)[1].split(",")]
     assert fields == [f[0] for f in kdt.kdt_server_info._fields_]
+
+
+def test_sharded_build_refuses_leaf_mode_and_bad_shard_counts_on_the_host(lib):
+    """kdt_build_sharded validates before it touches a device: leaf mode, the
+    estimator and shard counts outside 1..16 are invalid arguments."""
+    from paper_2201_08288_gb300 import kdt
+    i32 = ctypes.c_int32(0)
+    fake = ctypes.c_void_p(4096)  # never dereferenced: the call returns first
+    for kw, shards in ((dict(depth=0, leaf_size=8), 2), (dict(depth=4, fourier_j=4), 2), (dict(depth=4), 0),
+                       (dict(depth=4), 17)):
+        p = kdt.make_params(1000, 3, r=4, **kw)
+        assert lib.kdt_build_sharded(fake, ctypes.byref(p), shards, fake, fake, fake, fake, ctypes.byref(i32),
+                                     None) == 1
