@@ -343,6 +343,39 @@ kdt_status kdt_build_sharded(const float *points, const kdt_params *p, int32_t s
                              float *out_split_vals, int8_t *out_split_dims, int64_t *out_node_offsets,
                              int32_t *out_levels, void *stream);
 
+/* ---- queries on a built tree ----------------------------------------------
+ * The searches a k-d tree is built for (Sec. 1): only the cells a query's
+ * region can reach are visited. The tree is a build's output: points (device,
+ * float32 SoA [d][n], the build's input), perm, split_vals, split_dims and
+ * node_offsets (device) and L = levels. Query arrays are device SoA [d][nq].
+ * One CUDA thread per query; the call returns when the results are written.
+ * Errors: KDT_ERR_INVALID_ARG (sizes out of range, missing pointers),
+ *         KDT_ERR_CUDA. */
+
+/* Box query: point i is inside query q when lo[j][q] <= x_j(i) <= hi[j][q] for
+ * every coordinate j, comparing as the build does (float order with -0.0
+ * below +0.0). out_count [nq]: the number of points inside. out_list (device
+ * [nq][list_cap], or NULL): the original indices of the first list_cap points
+ * found (in no particular order; out_count may exceed list_cap). */
+kdt_status kdt_query_box(const float *points, int64_t n, int32_t d, const uint32_t *perm,
+                         const float *split_vals, const int8_t *split_dims, const int64_t *node_offsets,
+                         int32_t levels, const float *lo, const float *hi, int32_t nq, uint32_t *out_count,
+                         uint32_t *out_list, uint32_t list_cap, void *stream);
+
+/* Largest k of kdt_query_knn. */
+#define KDT_KNN_MAX_K 32
+
+/* k nearest neighbours of each query (1 <= k <= KDT_KNN_MAX_K): out_idx
+ * [nq][k] original indices and out_dist2 [nq][k] squared Euclidean distances
+ * (float64: each coordinate's difference and square rounded to double, summed
+ * over j = 0..d-1 in order, no fused multiply-add), nearest first, ties by the
+ * smaller index. With fewer than k points, the remaining entries hold index
+ * 0xffffffff and distance +inf. */
+kdt_status kdt_query_knn(const float *points, int64_t n, int32_t d, const uint32_t *perm,
+                         const float *split_vals, const int8_t *split_dims, const int64_t *node_offsets,
+                         int32_t levels, const float *queries, int32_t nq, int32_t k, uint32_t *out_idx,
+                         double *out_dist2, void *stream);
+
 /* ---- fault injection ----------------------------------------------------
  * Host-side hooks that make a failure happen on purpose, so that the error
  * paths can be tested without faulting a GPU. All are off by default; each

@@ -255,3 +255,39 @@ def fourier_cell_bounds(split_vals: np.ndarray, heap: int, d: int) -> tuple[floa
                 a = max(a, v)
         h = par
     return a, b
+
+
+# ------------------------------------------- queries on the point set
+# (Sec. 1: the searches the tree serves). Their definitions written out by
+# brute force over every point; the tree plays no part.
+
+def order_keys(x: np.ndarray) -> np.ndarray:
+    """The order-preserving key of float32 values (-0.0 below +0.0), as uint64."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return np.where(b >> 31 == 1, b ^ 0xFFFFFFFF, b | 0x80000000)
+
+
+def box_members(points: np.ndarray, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
+    """Original indices of the points with key(lo_j) <= key(x_j) <= key(hi_j)
+    for every coordinate j (points [d, n], lo and hi [d])."""
+    k = order_keys(points)
+    inside = np.all((order_keys(lo)[:, None] <= k) & (k <= order_keys(hi)[:, None]), axis=0)
+    return np.nonzero(inside)[0]
+
+
+def squared_distances(points: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """Per point: sum over j = 0..d-1, in that order, of the float64 square of
+    the float64 difference of coordinate j (each step rounded to double)."""
+    d2 = np.zeros(points.shape[1], np.float64)
+    for j in range(points.shape[0]):
+        diff = points[j].astype(np.float64) - np.float64(q[j])
+        d2 = d2 + diff * diff
+    return d2
+
+
+def nearest(points: np.ndarray, q: np.ndarray, k: int):
+    """The k nearest points to q: (indices, squared distances), nearest first,
+    ties by the smaller index."""
+    d2 = squared_distances(points, q)
+    order = np.lexsort((np.arange(d2.size), d2))[:k]
+    return order, d2[order]

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkdt.so")
 SOURCES = ["kdt_step.cu", "kdt_scatter.cu", "kdt_subtree.cu", "kdt_leafsort.cu", "kdt_engine.cu", "kdt_api.cu",
-           "kdt_trace.cu", "kdt_batched.cu", "kdt_server.cu", "kdt_noalloc.cu", "kdt_tune.cu", "kdt_fault.cu", "kdt_shard.cu"]
+           "kdt_trace.cu", "kdt_batched.cu", "kdt_server.cu", "kdt_noalloc.cu", "kdt_tune.cu", "kdt_fault.cu", "kdt_shard.cu", "kdt_query.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Werror", "all-warnings", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "-I", CSRC]

@@ -17,7 +17,7 @@ const char* const kNames[K_NUM] = {
     "k_part_scan",  "k_classify",   "k_part_scatter", "k_child_dims",  "k_subtree",
     "k_finalize",   "k_iota",       "k_leaf_sort",  "k_leaf_hist",   "k_leaf_scan",   "k_leaf_scatter",
     "k_leaf_copy",  "k_fourier_moments", "k_fourier_split", "k_shard_exchange", "k_shard_split",
-    "k_shard_merge"};
+    "k_shard_merge", "k_query"};
 
 struct Pending {
   KernelId id;

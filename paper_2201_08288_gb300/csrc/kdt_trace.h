@@ -15,7 +15,7 @@ enum KernelId {
   K_SELECT_TINY, K_SELECT_SMALL, K_SELECT_BIG, K_COMBINE, K_PART_COUNT, K_PART_SCAN, K_CLASSIFY, K_PART_SCATTER,
   K_CHILD_DIMS, K_SUBTREE, K_FINALIZE, K_IOTA, K_LEAF_SORT, K_LEAF_HIST, K_LEAF_SCAN,
   K_LEAF_SCATTER, K_LEAF_COPY, K_FOURIER_MOMENTS, K_FOURIER_SPLIT, K_SHARD_EXCHANGE, K_SHARD_SPLIT,
-  K_SHARD_MERGE, K_NUM
+  K_SHARD_MERGE, K_QUERY, K_NUM
 };
 
 // Launches replayed by a graph beyond the ones counted while it was captured.

@@ -42,7 +42,9 @@ EXPORTED = ["kdt_workspace_size", "kdt_build", "kdt_workspace_size_host", "kdt_b
             "kdt_trace_read", "kdt_build_noalloc", "kdt_workspace_size_batched", "kdt_build_batched",
             "kdt_server_create", "kdt_server_submit", "kdt_server_poll", "kdt_server_stats",
             "kdt_server_destroy", "kdt_server_cancel", "kdt_tuning_default", "kdt_set_tuning", "kdt_get_tuning",
-            "kdt_autotune", "kdt_fault_inject", "kdt_fault_clear", "kdt_build_sharded"]
+            "kdt_autotune", "kdt_fault_inject", "kdt_fault_clear", "kdt_build_sharded", "kdt_query_box",
+            "kdt_query_knn"]
+KDT_KNN_MAX_K = 32
 
 
 class KdtError(RuntimeError):
@@ -151,6 +153,11 @@ def load_library(path: str = LIB_PATH):
     lib.kdt_fault_inject.restype = ctypes.c_int
     lib.kdt_build_sharded.argtypes = [vp, P, ctypes.c_int32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), vp]
     lib.kdt_build_sharded.restype = ctypes.c_int
+    i64, i32 = ctypes.c_int64, ctypes.c_int32
+    lib.kdt_query_box.argtypes = [vp, i64, i32, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, ctypes.c_uint32, vp]
+    lib.kdt_query_box.restype = ctypes.c_int
+    lib.kdt_query_knn.argtypes = [vp, i64, i32, vp, vp, vp, vp, i32, vp, i32, i32, vp, vp, vp]
+    lib.kdt_query_knn.restype = ctypes.c_int
     lib.kdt_fault_clear.argtypes = []
     lib.kdt_fault_clear.restype = None
     lib.kdt_build_noalloc.argtypes = [vp, P, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), vp]
@@ -601,3 +608,53 @@ def fault_inject(kind: int, count: int) -> None:
 def fault_clear() -> None:
     """Turn every injected fault off (kdt_fault_clear)."""
     load_library().kdt_fault_clear()
+
+
+def _tree_args(points, tree):
+    import torch
+    if not (points.is_cuda and points.dtype == torch.float32 and points.is_contiguous() and points.dim() == 2):
+        raise ValueError("points must be the build's contiguous float32 CUDA tensor [d, n]")
+    d, n = points.shape
+    return (points.data_ptr(), n, d, tree.perm.data_ptr(), tree.split_vals.data_ptr(), tree.split_dims.data_ptr(),
+            tree.node_offsets.data_ptr(), tree.levels)
+
+
+def kdt_query_box(points, tree: Tree, lo, hi, *, list_cap: int = 0, stream=None):
+    """Points of a built tree inside each box (kdt_query_box). points: the
+    build's input (CUDA float32 [d, n]); tree: its Tree; lo, hi: CUDA float32
+    [d, nq]. Returns (counts int32 [nq], lists int32 [nq, list_cap] or None)."""
+    import torch
+    nq = lo.shape[1]
+    dev = points.device
+    counts = torch.empty(max(nq, 1), dtype=torch.int32, device=dev)
+    lists = torch.full((max(nq, 1), list_cap), -1, dtype=torch.int32, device=dev) if list_cap else None
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    lo, hi = lo.contiguous(), hi.contiguous()  # held until the call returns
+    with torch.cuda.device(dev):
+        st = load_library().kdt_query_box(*_tree_args(points, tree), lo.data_ptr(),
+                                          hi.data_ptr(), nq, counts.data_ptr(),
+                                          lists.data_ptr() if lists is not None else None, list_cap,
+                                          stream.cuda_stream)
+    if st:
+        raise KdtError(st, "kdt_query_box")
+    return counts[:nq], (lists[:nq] if lists is not None else None)
+
+
+def kdt_query_knn(points, tree: Tree, queries, k: int, *, stream=None):
+    """k nearest neighbours (kdt_query_knn). queries: CUDA float32 [d, nq].
+    Returns (indices int32 [nq, k], squared distances float64 [nq, k])."""
+    import torch
+    nq = queries.shape[1]
+    dev = points.device
+    idx = torch.empty((max(nq, 1), k), dtype=torch.int32, device=dev)
+    d2 = torch.empty((max(nq, 1), k), dtype=torch.float64, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    queries = queries.contiguous()  # held until the call returns
+    with torch.cuda.device(dev):
+        st = load_library().kdt_query_knn(*_tree_args(points, tree), queries.data_ptr(), nq, k,
+                                          idx.data_ptr(), d2.data_ptr(), stream.cuda_stream)
+    if st:
+        raise KdtError(st, "kdt_query_knn")
+    return idx[:nq], d2[:nq]
