@@ -393,6 +393,8 @@ def main() -> None:
     ap.add_argument("--load", type=float, default=0.7, help="c5: arrival rate / solo capacity")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shards", type=int, default=0,
+                    help="> 0: time the sharded build (kdt_build_sharded, this many logical shards; depth mode)")
     ap.add_argument("--no-extra", action="store_true",
                     help="c3: skip the batched (config 4) and served (config 5) sub-records")
     ap.add_argument("--extra-requests", type=int, default=3000,
@@ -443,6 +445,9 @@ def main() -> None:
                    torch.empty((1 << cap) + 1, dtype=torch.int64, device=dev), 0)
 
     def build_once():
+        if args.shards:
+            return kdt.kdt_build_sharded(pts, args.shards, sid=sid, outputs=out, stream=stream,
+                                         **{k: kw[k] for k in ("r", "subset_mode", "depth", "key_rule")})
         return kdt.kdt_build(pts, sid=sid, workspace=ws, outputs=out, stream=stream, **kw)
 
     for _ in range(args.warmup):
@@ -544,7 +549,7 @@ def main() -> None:
         cpu = cpu_baseline(args.workload)
 
     extra = {}
-    if args.workload == "c3" and world == 1 and not args.no_extra:
+    if args.workload == "c3" and world == 1 and not args.no_extra and not args.shards:
         # the batching and serving patterns on their own configurations, beside
         # the plain build: all 4096 trees of config 4 against the same trees
         # built one by one, and config 5's stream (its first N arrivals)
@@ -575,6 +580,7 @@ def main() -> None:
                        "subset_mode": ["mod", "contiguous", "explicit"][spec.subset_mode],
                        "key_rule": ["cyclic", "widest_spread"][spec.key_rule], "depth": spec.depth,
                        "levels": levels, "parallelism": f"replicas{world}",
+                       **({"shards": args.shards} if args.shards else {}),
                        "l2": f"inputs larger than L2 ({spec.d * spec.n * 4 / 1e9:.1f} GB per step)"},
             "roofline": roofline,
             "build_model_gbs": build_model_gbs, "build_model_frac": build_model_gbs / peak,

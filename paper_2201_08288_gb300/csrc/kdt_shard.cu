@@ -441,6 +441,7 @@ kdt_status sharded_build(const float* points, const kdt_params& p, int32_t G, ui
     pg[g].subset_id8 = out_bytes == 1 ? &kPlanId : nullptr;
     pg[g].subset_id16 = out_bytes == 2 ? (const uint16_t*)&kPlanId : nullptr;
     tp[g] = plan_tree(pg[g], /*no_subtree=*/true);
+    tp[g].leafsort = false;  // the merged leaves are sorted once, at the end (the subset-order presort stays)
     needs.add(pg[g], tp[g]);
   }
   const StepPlan sp = plan_step(needs);
