@@ -27,6 +27,8 @@ KEY_WIDEST_SPREAD = 1
 SUBSET_MOD = 0
 SUBSET_CONTIGUOUS = 1
 SUBSET_EXPLICIT = 2
+COMBINE_WEIGHTED = 0
+COMBINE_UNWEIGHTED = 1
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NAN_INPUT", 3: "OOM", 7: "LEVEL_CAP"}
 
@@ -49,6 +51,7 @@ class _Params(ctypes.Structure):
         ("leaf_size", ctypes.c_int32),
         ("max_levels", ctypes.c_int32),
         ("key_rule", ctypes.c_int32),
+        ("combine", ctypes.c_int32),
     ]
 
 
@@ -124,7 +127,7 @@ class Tree:
 
 
 def _params(points: np.ndarray, r: int, subset_mode: int, sid, depth: int, leaf_size: int,
-            max_levels: int, key_rule: int):
+            max_levels: int, key_rule: int, combine_rule: int = 0):
     d, n = points.shape
     p = _Params()
     p.n, p.d, p.subset_mode, p.r = n, d, subset_mode, r
@@ -140,18 +143,19 @@ def _params(points: np.ndarray, r: int, subset_mode: int, sid, depth: int, leaf_
         else:
             raise TypeError("subset ids must be uint8 or uint16")
     p.depth, p.leaf_size, p.max_levels, p.key_rule = depth, leaf_size, max_levels, key_rule
+    p.combine = combine_rule
     return p, keep
 
 
 def build_tree(points: np.ndarray, *, r: int = 1, subset_mode: int = SUBSET_MOD, sid=None,
                depth: int = 0, leaf_size: int = 1, max_levels: int = 20,
-               key_rule: int = KEY_CYCLIC) -> Tree:
+               key_rule: int = KEY_CYCLIC, combine_rule: int = COMBINE_WEIGHTED) -> Tree:
     """Build with the plain CPU reference. points: float32 [d, n] (SoA)."""
     points = np.ascontiguousarray(points, dtype=np.float32)
     if points.ndim != 2:
         raise ValueError("points must be [d, n]")
     d, n = points.shape
-    p, keep = _params(points, r, subset_mode, sid, depth, leaf_size, max_levels, key_rule)
+    p, keep = _params(points, r, subset_mode, sid, depth, leaf_size, max_levels, key_rule, combine_rule)
     cap = depth if depth > 0 else max_levels
     cap = max(0, min(cap, 30))
     perm = np.zeros(max(n, 1), np.uint32)
@@ -170,13 +174,14 @@ def build_tree(points: np.ndarray, *, r: int = 1, subset_mode: int = SUBSET_MOD,
 
 
 def split_cell(points: np.ndarray, idx: np.ndarray, level: int, *, r: int = 1,
-               subset_mode: int = SUBSET_MOD, sid=None, key_rule: int = KEY_CYCLIC):
+               subset_mode: int = SUBSET_MOD, sid=None, key_rule: int = KEY_CYCLIC,
+               combine_rule: int = COMBINE_WEIGHTED):
     """Split of one cell whose points have original indices ``idx``.
 
     Returns (dim, key, value, left_count)."""
     points = np.ascontiguousarray(points, dtype=np.float32)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
-    p, keep = _params(points, r, subset_mode, sid, 1, 1, 1, key_rule)
+    p, keep = _params(points, r, subset_mode, sid, 1, 1, 1, key_rule, combine_rule)
     dim, k, v, left = ctypes.c_int32(), ctypes.c_uint32(), ctypes.c_float(), ctypes.c_int64()
     st = _load().kdto_split_cell(points.ctypes.data, ctypes.byref(p), idx.ctypes.data,
                                  idx.size, level, ctypes.byref(dim), ctypes.byref(k),

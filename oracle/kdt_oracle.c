@@ -29,6 +29,9 @@
  *   R7  widest spread = the range (double)max - (double)min of the cell's
  *       points per coordinate (0 when max and min are the same key); the
  *       lowest coordinate wins ties (Sec. 1, widest-dispersion rule);
+ *   R2u (combine = KDTO_COMBINE_UNWEIGHTED) every non-empty subset counts
+ *       once: the split is the lower median, rank (m-1)/2 in (key, subset)
+ *       order, of the m subset medians (the plain median of medians);
  *   R8  leaf mode: a cell is terminal when it holds <= leaf_size points, or
  *       when its last s splits each left the right child empty, s = d for
  *       cyclic keys and s = 1 for widest spread (its point set can no longer
@@ -77,6 +80,8 @@ static int validate(const float *points, const kdto_params *p) {
   if (p->d < 1 || p->d > 64) return KDTO_ERR_INVALID_ARG;
   if (p->r < 1 || p->r > 65536) return KDTO_ERR_INVALID_ARG;
   if (p->key_rule != KDTO_KEY_CYCLIC && p->key_rule != KDTO_KEY_WIDEST_SPREAD)
+    return KDTO_ERR_INVALID_ARG;
+  if (p->combine != KDTO_COMBINE_WEIGHTED && p->combine != KDTO_COMBINE_UNWEIGHTED)
     return KDTO_ERR_INVALID_ARG;
   if (p->depth < 0 || p->depth > KDTO_MAX_LEVELS) return KDTO_ERR_INVALID_ARG;
   if (p->depth == 0) {
@@ -164,13 +169,18 @@ static int split_key(const float *pts, const kdto_params *p, const int64_t *idx,
     b = e;
   }
 
-  /* step 2: first pair in (key, sid) order whose cumulative count reaches half */
+  /* step 2: first pair in (key, sid) order whose cumulative count reaches
+   * half (R2), or the pair at rank (npairs-1)/2 when every subset counts once (R2u) */
   qsort(mp, (size_t)npairs, sizeof *mp, cmp_med_pair);
-  int64_t cum = 0;
   uint32_t chosen = mp[npairs - 1].key;
-  for (int64_t j = 0; j < npairs; ++j) {
-    cum += mp[j].w;
-    if (2 * cum >= cnt) { chosen = mp[j].key; break; }
+  if (p->combine == KDTO_COMBINE_UNWEIGHTED) {
+    chosen = mp[(npairs - 1) / 2].key;
+  } else {
+    int64_t cum = 0;
+    for (int64_t j = 0; j < npairs; ++j) {
+      cum += mp[j].w;
+      if (2 * cum >= cnt) { chosen = mp[j].key; break; }
+    }
   }
   *out_key = chosen;
   free(sk);

@@ -54,7 +54,11 @@ typedef struct {
   int32_t leaf_size;       /* leaf mode: cells with count <= leaf_size terminate  */
   int32_t max_levels;      /* leaf mode: cap on the number of split levels        */
   int32_t key_rule;        /* KDTO_KEY_*                                          */
+  int32_t combine;         /* KDTO_COMBINE_*                                      */
 } kdto_params;
+
+/* How a cell's split is formed from its subsets' lower medians (R2 / R2u). */
+enum { KDTO_COMBINE_WEIGHTED = 0, KDTO_COMBINE_UNWEIGHTED = 1 };
 
 /* Order-preserving float -> uint32 key and its inverse. */
 uint32_t kdto_key(float x);

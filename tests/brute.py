@@ -53,19 +53,20 @@ def widest_dim(cols, pts):
     return best
 
 
-def split(cols, sids, pts, level, key_rule):
-    """(dim, value) of a non-empty cell given its point indices."""
+def split(cols, sids, pts, level, key_rule, combine_rule=0):
+    """(dim, value) of a non-empty cell given its point indices; with
+    combine_rule 1 every subset weighs one."""
     d = len(cols)
     t = level % d if key_rule == 0 else widest_dim(cols, pts)
     groups = {}
     for i in pts:
         groups.setdefault(sids[i], []).append(cols[t][i])
-    meds = [(lower_median(v), len(v)) for v in groups.values()]
+    meds = [(lower_median(v), 1 if combine_rule else len(v)) for v in groups.values()]
     return t, combine(meds)
 
 
 def build(points, *, r=1, subset_mode=0, sid=None, depth=0, leaf_size=1, max_levels=20,
-          key_rule=0):
+          key_rule=0, combine_rule=0):
     """Returns (perm, split_vals, split_dims, node_offsets, L) as Python lists."""
     cols = [[float(v) for v in row] for row in points]
     d = len(cols)
@@ -83,7 +84,7 @@ def build(points, *, r=1, subset_mode=0, sid=None, depth=0, leaf_size=1, max_lev
         """(dim, value, left, right, child_stall) of one node."""
         if terminal(pts, stall):
             return -1, math.inf, pts, [], stall
-        t, m = split(cols, sids, pts, level, key_rule)
+        t, m = split(cols, sids, pts, level, key_rule, combine_rule)
         left = [i for i in pts if order_key(cols[t][i]) <= order_key(m)]
         right = [i for i in pts if order_key(cols[t][i]) > order_key(m)]
         return t, m, left, right, (stall + 1 if not right else 0)

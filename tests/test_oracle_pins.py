@@ -348,3 +348,51 @@ def test_split_cell_agrees_with_build():
         lb, le, _ = node_range(t.node_offsets, 5, 2 * h + 1)
         assert left == le - lb
         assert np.all(le_total(pts[dim, t.perm[lb:le].astype(np.int64)], v))
+
+
+# ------------------------------------- the unweighted rule (R2u, NEXT-4)
+
+
+def test_unweighted_rule_hand_example():
+    """One subset of seven points (median 4) and two singletons (10, 11): the
+    count-weighted rule splits at 4 (7 of 9 points reach half), the
+    unweighted one at the middle of the medians 4, 10, 11, i.e. 10."""
+    pts = np.array([[1, 2, 3, 4, 5, 6, 7, 10, 11]], np.float32)
+    sid = np.array([0] * 7 + [1, 2], np.uint8)
+    w = oracle.build_tree(pts, r=3, subset_mode=2, sid=sid, depth=1)
+    u = oracle.build_tree(pts, r=3, subset_mode=2, sid=sid, depth=1, combine_rule=oracle.COMBINE_UNWEIGHTED)
+    assert float(w.split_vals[0]) == 4.0 and w.node_offsets.tolist() == [0, 4, 9]
+    assert float(u.split_vals[0]) == 10.0 and u.node_offsets.tolist() == [0, 8, 9]
+    # an even number of medians takes the lower one: 4 and 10 -> 4
+    u2 = oracle.build_tree(pts[:, :8], r=2, subset_mode=2, sid=sid[:8], depth=1,
+                           combine_rule=oracle.COMBINE_UNWEIGHTED)
+    assert float(u2.split_vals[0]) == 4.0
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_unweighted_rule_against_brute_force(seed):
+    rng = np.random.default_rng(5000 + seed)
+    n = int(rng.integers(0, 100))
+    d = int(rng.integers(1, 4))
+    r = int(rng.integers(1, 10))
+    pts = (rng.integers(-3, 4, size=(d, n)).astype(np.float32) if seed % 2
+           else rng.standard_normal((d, n)).astype(np.float32))
+    sid = rng.integers(0, r, n).astype(np.uint8)
+    kw = dict(r=r, subset_mode=2, sid=sid, key_rule=seed % 2, combine_rule=oracle.COMBINE_UNWEIGHTED)
+    if seed % 3:
+        _compare_with_brute(pts, depth=int(rng.integers(1, 6)), **kw)
+    else:
+        _compare_with_brute(pts, depth=0, leaf_size=int(rng.integers(1, 6)), max_levels=24, **kw)
+
+
+def test_unweighted_rule_equals_weighted_for_one_subset_and_for_singletons():
+    """With one subset, or with every point its own subset, every subset has
+    the same size in every cell, and both rules take the lower median."""
+    rng = np.random.default_rng(9)
+    pts = rng.standard_normal((3, 3000)).astype(np.float32)
+    for kw in (dict(r=1, depth=8), dict(r=3000, subset_mode=2,
+                                          sid=np.arange(3000).astype(np.uint16), depth=8)):
+        a = oracle.build_tree(pts, **kw)
+        b = oracle.build_tree(pts, combine_rule=oracle.COMBINE_UNWEIGHTED, **kw)
+        assert np.array_equal(a.perm, b.perm) and np.array_equal(a.split_vals.view(np.uint32),
+                                                                  b.split_vals.view(np.uint32))
