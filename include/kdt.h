@@ -79,6 +79,16 @@ typedef enum kdt_subset_mode {
 /* Largest accepted dimension. */
 #define KDT_MAX_DIMS 64
 
+/* How a cell's split is formed from the lower medians of its (cell, subset)
+ * segments. WEIGHTED: the smallest subset median m such that the subsets
+ * whose median is <= m hold at least half of the cell's points (each subset
+ * weighs its size; the library's default). UNWEIGHTED: every non-empty subset
+ * counts once, the split is the lower median (rank (m-1)/2 of m, ties by
+ * subset id) of the subset medians, the plain median of medians. The paper
+ * combines additive moments instead (Sec. 3.2); both rules are the
+ * library's. */
+typedef enum { KDT_COMBINE_WEIGHTED = 0, KDT_COMBINE_UNWEIGHTED = 1 } kdt_combine_rule;
+
 typedef struct kdt_params {
   int64_t n;                     /* points, 0 <= n <= 2^32 - 1                          */
   int32_t d;                     /* coordinates per point, 1..64                        */
@@ -97,6 +107,8 @@ typedef struct kdt_params {
                                  /* mode, every coordinate in (0,1); plain builds only;    */
                                  /* subsets do not change its sums, so r and the ids are   */
                                  /* ignored)                                               */
+  int32_t combine_rule;          /* kdt_combine_rule: how a cell's split is formed from its */
+                                 /* subsets' lower medians (ignored when fourier_j > 0)    */
 } kdt_params;
 
 /* Largest fourier_j. */

@@ -79,6 +79,8 @@ kdt_status validate_params(const kdt_params* p) {
     if (p->max_levels < 0 || p->max_levels > KDT_MAX_LEVELS) return KDT_ERR_INVALID_ARG;
   }
   if (p->fourier_j < 0 || p->fourier_j > KDT_FOURIER_MAX_J) return KDT_ERR_INVALID_ARG;
+  if (p->combine_rule != KDT_COMBINE_WEIGHTED && p->combine_rule != KDT_COMBINE_UNWEIGHTED)
+    return KDT_ERR_INVALID_ARG;
   if (p->fourier_j > 0 && (p->key_rule != KDT_KEY_CYCLIC || p->depth == 0)) return KDT_ERR_INVALID_ARG;
   return KDT_OK;
 }
@@ -279,6 +281,7 @@ kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p
   h.leaf_size = p.leaf_size;
   h.max_levels = p.max_levels;
   h.fourier_j = p.fourier_j;
+  h.combine_rule = p.combine_rule;
   h.stall_limit = p.key_rule == KDT_KEY_CYCLIC ? p.d : 1;
   h.sid_bytes = tp.sid_bytes;
   h.small_max = tp.small_max;

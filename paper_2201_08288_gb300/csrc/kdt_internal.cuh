@@ -79,6 +79,8 @@ struct TreeDev {
   uint32_t* huge_count;  // device word
   uint32_t huge_cap;
   int32_t fourier_j;     // > 0: splits by the Fourier-moment estimator with this many harmonics
+  int32_t combine_rule;  // 0: count-weighted median of the subset medians; 1: every subset counts once
+  int32_t pad0;
   uint32_t* out_perm;
   float* out_vals;
   int8_t* out_dims;

@@ -869,7 +869,19 @@ __device__ __forceinline__ void combine_cell(const TreeDev* trees, const StepDev
   const TreeDev& t = trees[cell.tree];
   const int r = t.r;
   const uint32_t g0 = s.seg_base[c];
+  const bool unit = t.combine_rule == 1;  // every non-empty subset counts once
   uint32_t rank = (cell_weight(s, c, cell) - 1) / 2, prefix = 0, mask = 0;
+  if (unit) {  // rank (m - 1) / 2 among the m non-empty segments
+    if (threadIdx.x == 0) bcast[0] = 0;
+    __syncthreads();
+    uint32_t m = 0;
+    for (int j = threadIdx.x; j < r; j += blockDim.x) m += s.seg_w[g0 + j] != 0u;
+    m = warp_sum(m);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&bcast[0], m);
+    __syncthreads();
+    rank = (bcast[0] - 1u) / 2u;
+    __syncthreads();
+  }
   for (int shift = 24; shift >= 0; shift -= 8) {
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
@@ -877,7 +889,7 @@ __device__ __forceinline__ void combine_cell(const TreeDev* trees, const StepDev
       const uint32_t w = s.seg_w[g0 + j];
       if (!w) continue;
       const uint32_t k = s.seg_med[g0 + j];
-      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], w);
+      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], unit ? 1u : w);
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -920,9 +932,16 @@ __device__ __forceinline__ void combine_warp_cell(const TreeDev* trees, const St
   const uint32_t g0 = s.seg_base[c];
   const uint32_t* med = s.seg_med + g0;
   const uint32_t* wt = s.seg_w + g0;
+  const bool unit = t.combine_rule == 1;  // every non-empty subset counts once
+  uint32_t rank = (cell_weight(s, c, cell) - 1) / 2;
+  if (unit) {
+    uint32_t nz = 0;
+    for (uint32_t j = lane; j < (uint32_t)t.r; j += 32) nz += wt[j] != 0u;
+    rank = (warp_sum(nz) - 1u) / 2u;
+  }
   const uint32_t m = warp_weighted_select(
-      (uint32_t)t.r, (cell_weight(s, c, cell) - 1) / 2, hist[warp], [&](uint32_t j) { return med[j]; },
-      [&](uint32_t j) { return wt[j]; }, [&](uint32_t j) { return wt[j] != 0u; });
+      (uint32_t)t.r, rank, hist[warp], [&](uint32_t j) { return med[j]; },
+      [&](uint32_t j) { return unit ? 1u : wt[j]; }, [&](uint32_t j) { return wt[j] != 0u; });
   if (lane == 0) {
     s.mkey[c] = m;
     t.out_vals[cell.heap] = key_float(m);

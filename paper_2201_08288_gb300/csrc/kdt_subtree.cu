@@ -603,9 +603,12 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
         for (uint32_t k = warp; k < ncur; k += NW) {
           const uint32_t b = cc[k].begin, e = b + cc[k].count;
           const uint32_t s0 = S.pre[b], s1 = S.pre[e], ns = s1 - s0;
-          const uint32_t rank = (cc[k].count - 1u) / 2u;
+          const bool unit = t.combine_rule == 1;  // every subset counts once (segments are non-empty)
+          const uint32_t rank = unit ? (ns - 1u) / 2u : (cc[k].count - 1u) / 2u;
           auto key_of = [&](uint32_t j) { return S.smed[s0 + j]; };
-          auto w_of = [&](uint32_t j) { return min((uint32_t)S.segs[s0 + j + 1], e) - S.segs[s0 + j]; };
+          auto w_of = [&](uint32_t j) {
+            return unit ? 1u : min((uint32_t)S.segs[s0 + j + 1], e) - S.segs[s0 + j];
+          };
           uint32_t m;
           if (ns <= 32u)
             m = warp_wsel_bits<1>(ns, rank, key_of, w_of);

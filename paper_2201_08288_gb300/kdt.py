@@ -22,6 +22,8 @@ KDT_KEY_WIDEST_SPREAD = 1
 KDT_SUBSET_MOD = 0
 KDT_SUBSET_CONTIGUOUS = 1
 KDT_SUBSET_EXPLICIT = 2
+KDT_COMBINE_WEIGHTED = 0
+KDT_COMBINE_UNWEIGHTED = 1
 KDT_MAX_LEVELS = 30
 KDT_MAX_SUBSETS = 4096
 
@@ -71,6 +73,7 @@ class kdt_params(ctypes.Structure):
         ("leaf_size", ctypes.c_int32),
         ("max_levels", ctypes.c_int32),
         ("fourier_j", ctypes.c_int32),
+        ("combine_rule", ctypes.c_int32),
     ]
 
 
@@ -183,12 +186,14 @@ def load_library(path: str = LIB_PATH):
 
 def make_params(n: int, d: int, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid_ptr: int = 0,
                 sid_bytes: int = 1, depth: int = 0, leaf_size: int = 1, max_levels: int = 20,
-                key_rule: int = KDT_KEY_CYCLIC, fourier_j: int = 0) -> kdt_params:
+                key_rule: int = KDT_KEY_CYCLIC, fourier_j: int = 0,
+                combine_rule: int = KDT_COMBINE_WEIGHTED) -> kdt_params:
     p = kdt_params()
     p.n, p.d, p.subset_mode, p.r, p.key_rule = n, d, subset_mode, r, key_rule
     p.subset_id8 = sid_ptr if (sid_ptr and sid_bytes == 1) else None
     p.subset_id16 = sid_ptr if (sid_ptr and sid_bytes == 2) else None
     p.depth, p.leaf_size, p.max_levels, p.fourier_j = depth, leaf_size, max_levels, fourier_j
+    p.combine_rule = combine_rule
     return p
 
 
@@ -259,20 +264,24 @@ def _sid_info(sid):
 
 def kdt_build(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None, depth: int = 0,
               leaf_size: int = 1, max_levels: int = 20, key_rule: int = KDT_KEY_CYCLIC,
-              workspace=None, stream=None, outputs: Optional[Tree] = None, fourier_j: int = 0) -> Tree:
+              workspace=None, stream=None, outputs: Optional[Tree] = None, fourier_j: int = 0,
+              combine_rule: int = KDT_COMBINE_WEIGHTED) -> Tree:
     """Build on the device. points: torch float32 CUDA tensor [d, n], contiguous.
     sid: uint8 (or int16 holding uint16) CUDA tensor [n] for explicit subsets.
     workspace: optional uint8 CUDA tensor of >= kdt_workspace_size bytes.
     outputs: optional preallocated Tree of tensors (sized for the capacity).
     fourier_j > 0: splits by the paper's Fourier-moment estimator with J
-    harmonics (cyclic keys, depth mode, coordinates in (0,1))."""
+    harmonics (cyclic keys, depth mode, coordinates in (0,1)).
+    combine_rule: KDT_COMBINE_WEIGHTED (the default) or KDT_COMBINE_UNWEIGHTED
+    (every non-empty subset's median counts once)."""
     import torch
     if not (points.is_cuda and points.dtype == torch.float32 and points.is_contiguous() and points.dim() == 2):
         raise ValueError("points must be a contiguous float32 CUDA tensor [d, n]")
     d, n = points.shape
     sid_ptr, sid_bytes = _sid_info(sid)
     p = make_params(n, d, r=r, subset_mode=subset_mode, sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth,
-                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule, fourier_j=fourier_j)
+                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule, fourier_j=fourier_j,
+                    combine_rule=combine_rule)
     lib = load_library()
     cap = _capacity(depth, max_levels)
     dev = points.device
@@ -301,7 +310,8 @@ def kdt_build(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None
 
 def kdt_build_host(points: np.ndarray, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None,
                    depth: int = 0, leaf_size: int = 1, max_levels: int = 20, key_rule: int = KDT_KEY_CYCLIC,
-                   workspace=None, stream=None, outputs=None, fourier_j: int = 0) -> Tree:
+                   workspace=None, stream=None, outputs=None, fourier_j: int = 0,
+                   combine_rule: int = KDT_COMBINE_WEIGHTED) -> Tree:
     """Build from HOST arrays (numpy, ideally pinned): copies in, builds, copies
     the outputs back into numpy arrays, all inside the library call."""
     import torch
@@ -312,7 +322,8 @@ def kdt_build_host(points: np.ndarray, *, r: int = 1, subset_mode: int = KDT_SUB
         sid = np.ascontiguousarray(sid)
         sid_ptr, sid_bytes = sid.ctypes.data, sid.dtype.itemsize
     p = make_params(n, d, r=r, subset_mode=subset_mode, sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth,
-                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule, fourier_j=fourier_j)
+                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule, fourier_j=fourier_j,
+                    combine_rule=combine_rule)
     cap = _capacity(depth, max_levels)
     if outputs is None:
         outputs = Tree(np.empty(max(n, 1), np.uint32), np.empty(max((1 << cap) - 1, 1), np.float32),
@@ -337,6 +348,7 @@ def kdt_build_host(points: np.ndarray, *, r: int = 1, subset_mode: int = KDT_SUB
 
 def kdt_build_noalloc(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None, depth: int = 0,
                       leaf_size: int = 1, max_levels: int = 20, key_rule: int = KDT_KEY_CYCLIC, stream=None,
+                      combine_rule: int = KDT_COMBINE_WEIGHTED,
                       outputs: Tree) -> Tree:
     """kdt_build that allocates nothing: the library's fixed 64 MiB device
     scratch array is the workspace. outputs: preallocated Tree of tensors
@@ -347,7 +359,7 @@ def kdt_build_noalloc(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, 
     d, n = points.shape
     sid_ptr, sid_bytes = _sid_info(sid)
     p = make_params(n, d, r=r, subset_mode=subset_mode, sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth,
-                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule)
+                    leaf_size=leaf_size, max_levels=max_levels, key_rule=key_rule, combine_rule=combine_rule)
     if stream is None:
         stream = torch.cuda.current_stream(points.device)
     levels = ctypes.c_int32(0)
@@ -366,6 +378,7 @@ def kdt_build_noalloc(points, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, 
 
 def kdt_build_sharded(points, shards: int, *, r: int = 1, subset_mode: int = KDT_SUBSET_MOD, sid=None,
                       depth: int, key_rule: int = KDT_KEY_CYCLIC, stream=None,
+                      combine_rule: int = KDT_COMBINE_WEIGHTED,
                       outputs: Optional[Tree] = None) -> Tree:
     """The build emulated on `shards` logical shards (subset s on shard
     s % shards; per-level all-gather of the segment statistics), depth mode.
@@ -376,7 +389,7 @@ def kdt_build_sharded(points, shards: int, *, r: int = 1, subset_mode: int = KDT
     d, n = points.shape
     sid_ptr, sid_bytes = _sid_info(sid)
     p = make_params(n, d, r=r, subset_mode=subset_mode, sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth,
-                    key_rule=key_rule)
+                    key_rule=key_rule, combine_rule=combine_rule)
     dev = points.device
     if outputs is None:
         outputs = _alloc_outputs(n, depth, dev)
@@ -418,7 +431,8 @@ def make_descs(items, outputs=None):
         max_levels = it.get("max_levels", 20)
         p = make_params(n, d, r=it.get("r", 1), subset_mode=it.get("subset_mode", KDT_SUBSET_MOD),
                         sid_ptr=sid_ptr, sid_bytes=sid_bytes, depth=depth, leaf_size=it.get("leaf_size", 1),
-                        max_levels=max_levels, key_rule=it.get("key_rule", KDT_KEY_CYCLIC))
+                        max_levels=max_levels, key_rule=it.get("key_rule", KDT_KEY_CYCLIC),
+                        combine_rule=it.get("combine_rule", KDT_COMBINE_WEIGHTED))
         o = outputs[i] if outputs is not None else _alloc_outputs(n, _capacity(depth, max_levels), pts.device)
         outs.append(o)
         descs[i].points = pts.data_ptr()

@@ -46,7 +46,7 @@ def test_params_struct_layout_matches_header():
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"\*?\s*([a-z0-9_]+)\s*;", body)
     assert fields == [f[0] for f in kdt.kdt_params._fields_]
-    assert ctypes.sizeof(kdt.kdt_params) == 56
+    assert ctypes.sizeof(kdt.kdt_params) == 64
 
 
 def test_status_strings_and_capacity_need_no_gpu(lib):
