@@ -25,7 +25,6 @@
 // child's segments start (its left or right rank there), which is the
 // children's subset offset table.
 #include <algorithm>
-#include <type_traits>
 
 #include "kdt_internal.cuh"
 #include "kdt_launch.h"
@@ -338,123 +337,113 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         keep[q] = i < mcnt && !(left[q] ? term_left : term_right);
       }
 
-      // ---- the moves. A sub-tile that fills every consumer thread's items and
-      // whose children both stay in the pipeline (the usual case) takes a path
-      // without a condition per item.
-      auto move = [&](auto full) {
-        constexpr bool kFull = decltype(full)::value;
-        // ---- permutation
+      // ---- permutation
+#pragma unroll
+      for (int q = 0; q < kMaxItems; ++q) {
+        const uint32_t i = tid + q * kCT;
+        if (i >= mcnt) continue;
+        if (keep[q])
+          m.pout[dst[q]] = pa[i];
+        else
+          m.out_perm[dst[q]] = pa[i];
+      }
+
+      // ---- coordinate columns, two at a time, straight from shared memory
+#pragma unroll
+      for (int c = 0; c < d; c += 2) {
+        const bool two = c + 1 < d;
+        const uint32_t* a0 = A + (size_t)c * stride + m.ph[c];
+        const uint32_t* a1 = two ? A + (size_t)(c + 1) * stride + m.ph[c + 1] : a0;
+        float* o0 = m.xout + (int64_t)c * n;
+        float* o1 = m.xout + (int64_t)(c + 1) * n;
+        uint32_t v0[kMaxItems], v1[kMaxItems];
 #pragma unroll
         for (int q = 0; q < kMaxItems; ++q) {
           const uint32_t i = tid + q * kCT;
-          if (!kFull && i >= mcnt) continue;
-          if (kFull || keep[q])
-            m.pout[dst[q]] = pa[i];
-          else
-            m.out_perm[dst[q]] = pa[i];
+          v0[q] = i < mcnt ? a0[i] : 0u;
+          v1[q] = i < mcnt ? a1[i] : 0u;
         }
-
-        // ---- coordinate columns, two at a time, straight from shared memory
-#pragma unroll
-        for (int c = 0; c < d; c += 2) {
-          const bool two = c + 1 < d;
-          const uint32_t* a0 = A + (size_t)c * stride + m.ph[c];
-          const uint32_t* a1 = two ? A + (size_t)(c + 1) * stride + m.ph[c + 1] : a0;
-          float* o0 = m.xout + (int64_t)c * n;
-          float* o1 = m.xout + (int64_t)(c + 1) * n;
-          uint32_t v0[kMaxItems], v1[kMaxItems];
-#pragma unroll
-          for (int q = 0; q < kMaxItems; ++q) {
-            const uint32_t i = tid + q * kCT;
-            v0[q] = (kFull || i < mcnt) ? a0[i] : 0u;
-            v1[q] = (kFull || i < mcnt) ? a1[i] : 0u;
-          }
-          if (level0)
-#pragma unroll
-            for (int q = 0; q < kMaxItems; ++q)
-              saw_nan |= (kFull || tid + q * kCT < mcnt) &&
-                         (is_nan_bits(__uint_as_float(v0[q])) || is_nan_bits(__uint_as_float(v1[q])));
+        if (level0)
 #pragma unroll
           for (int q = 0; q < kMaxItems; ++q)
-            if (kFull || keep[q]) {
-              o0[dst[q]] = __uint_as_float(v0[q]);
-              if (two) o1[dst[q]] = __uint_as_float(v1[q]);
+            saw_nan |= (tid + q * kCT < mcnt) &&
+                       (is_nan_bits(__uint_as_float(v0[q])) || is_nan_bits(__uint_as_float(v1[q])));
+#pragma unroll
+        for (int q = 0; q < kMaxItems; ++q)
+          if (keep[q]) {
+            o0[dst[q]] = __uint_as_float(v0[q]);
+            if (two) o1[dst[q]] = __uint_as_float(v1[q]);
+          }
+        if (want_mm && kAcc) {
+          // min / max as floats (the widest rule only uses max - min, which -0
+          // and +0 do not change); keys are formed at the run's end
+          const int c1 = two ? c + 1 : c;
+#pragma unroll
+          for (int q = 0; q < kMaxItems; ++q)
+            if (keep[q]) {
+              const float x0 = __uint_as_float(v0[q]), x1 = __uint_as_float(v1[q]);
+              const int side = left[q] ? 0 : 1;
+              if (side == 0) {
+                acc[c % kAD][0][0] = fminf(acc[c % kAD][0][0], x0);
+                acc[c % kAD][0][1] = fmaxf(acc[c % kAD][0][1], x0);
+                if (two) {
+                  acc[c1 % kAD][0][0] = fminf(acc[c1 % kAD][0][0], x1);
+                  acc[c1 % kAD][0][1] = fmaxf(acc[c1 % kAD][0][1], x1);
+                }
+              } else {
+                acc[c % kAD][1][0] = fminf(acc[c % kAD][1][0], x0);
+                acc[c % kAD][1][1] = fmaxf(acc[c % kAD][1][1], x0);
+                if (two) {
+                  acc[c1 % kAD][1][0] = fminf(acc[c1 % kAD][1][0], x1);
+                  acc[c1 % kAD][1][1] = fmaxf(acc[c1 % kAD][1][1], x1);
+                }
+              }
             }
-          if (want_mm && kAcc) {
-            // min / max as floats (the widest rule only uses max - min, which -0
-            // and +0 do not change); keys are formed at the run's end
-            const int c1 = two ? c + 1 : c;
+        } else if (want_mm) {
+          // min / max as floats, then keys once per warp and sub-tile
+          float mm[2][2][2] = {{{inf, -inf}, {inf, -inf}}, {{inf, -inf}, {inf, -inf}}};  // [col][side][min,max]
 #pragma unroll
-            for (int q = 0; q < kMaxItems; ++q)
-              if (kFull || keep[q]) {
-                const float x0 = __uint_as_float(v0[q]), x1 = __uint_as_float(v1[q]);
-                const int side = left[q] ? 0 : 1;
-                if (side == 0) {
-                  acc[c % kAD][0][0] = fminf(acc[c % kAD][0][0], x0);
-                  acc[c % kAD][0][1] = fmaxf(acc[c % kAD][0][1], x0);
-                  if (two) {
-                    acc[c1 % kAD][0][0] = fminf(acc[c1 % kAD][0][0], x1);
-                    acc[c1 % kAD][0][1] = fmaxf(acc[c1 % kAD][0][1], x1);
-                  }
-                } else {
-                  acc[c % kAD][1][0] = fminf(acc[c % kAD][1][0], x0);
-                  acc[c % kAD][1][1] = fmaxf(acc[c % kAD][1][1], x0);
-                  if (two) {
-                    acc[c1 % kAD][1][0] = fminf(acc[c1 % kAD][1][0], x1);
-                    acc[c1 % kAD][1][1] = fmaxf(acc[c1 % kAD][1][1], x1);
-                  }
-                }
+          for (int q = 0; q < kMaxItems; ++q)
+            if (keep[q]) {
+              const float x0 = __uint_as_float(v0[q]), x1 = __uint_as_float(v1[q]);
+              if (left[q]) {
+                mm[0][0][0] = fminf(mm[0][0][0], x0);
+                mm[0][0][1] = fmaxf(mm[0][0][1], x0);
+                mm[1][0][0] = fminf(mm[1][0][0], x1);
+                mm[1][0][1] = fmaxf(mm[1][0][1], x1);
+              } else {
+                mm[0][1][0] = fminf(mm[0][1][0], x0);
+                mm[0][1][1] = fmaxf(mm[0][1][1], x0);
+                mm[1][1][0] = fminf(mm[1][1][0], x1);
+                mm[1][1][1] = fmaxf(mm[1][1][1], x1);
               }
-          } else if (want_mm) {
-            // min / max as floats, then keys once per warp and sub-tile
-            float mm[2][2][2] = {{{inf, -inf}, {inf, -inf}}, {{inf, -inf}, {inf, -inf}}};  // [col][side][min,max]
+            }
 #pragma unroll
-            for (int q = 0; q < kMaxItems; ++q)
-              if (kFull || keep[q]) {
-                const float x0 = __uint_as_float(v0[q]), x1 = __uint_as_float(v1[q]);
-                if (left[q]) {
-                  mm[0][0][0] = fminf(mm[0][0][0], x0);
-                  mm[0][0][1] = fmaxf(mm[0][0][1], x0);
-                  mm[1][0][0] = fminf(mm[1][0][0], x1);
-                  mm[1][0][1] = fmaxf(mm[1][0][1], x1);
-                } else {
-                  mm[0][1][0] = fminf(mm[0][1][0], x0);
-                  mm[0][1][1] = fmaxf(mm[0][1][1], x0);
-                  mm[1][1][0] = fminf(mm[1][1][0], x1);
-                  mm[1][1][1] = fmaxf(mm[1][1][1], x1);
-                }
-              }
+          for (int cc = 0; cc < 2; ++cc) {
+            if (cc == 1 && !two) break;
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-              if (cc == 1 && !two) break;
-#pragma unroll
-              for (int side = 0; side < 2; ++side) {
-                const uint32_t lo = __reduce_min_sync(0xffffffffu, ord_key(mm[cc][side][0]));
-                const uint32_t hi = __reduce_max_sync(0xffffffffu, ord_key(mm[cc][side][1]));
-                if (lane == 0) {
-                  atomic_min_shared(&tmm[side][c + cc][0], lo);
-                  atomic_max_shared(&tmm[side][c + cc][1], hi);
-                }
+            for (int side = 0; side < 2; ++side) {
+              const uint32_t lo = __reduce_min_sync(0xffffffffu, ord_key(mm[cc][side][0]));
+              const uint32_t hi = __reduce_max_sync(0xffffffffu, ord_key(mm[cc][side][1]));
+              if (lane == 0) {
+                atomic_min_shared(&tmm[side][c + cc][0], lo);
+                atomic_max_shared(&tmm[side][c + cc][1], hi);
               }
             }
           }
         }
-        if (explicit_sid) {
+      }
+      if (explicit_sid) {
 #pragma unroll
-          for (int q = 0; q < kMaxItems; ++q) {
-            const uint32_t i = tid + q * kCT;
-            if (!kFull && !keep[q]) continue;
-            if (m.sid_bytes == 1)
-              ((uint8_t*)m.sout)[dst[q]] = SA[i];
-            else
-              ((uint16_t*)m.sout)[dst[q]] = ((const uint16_t*)SA)[i];
-          }
+        for (int q = 0; q < kMaxItems; ++q) {
+          const uint32_t i = tid + q * kCT;
+          if (!keep[q]) continue;
+          if (m.sid_bytes == 1)
+            ((uint8_t*)m.sout)[dst[q]] = SA[i];
+          else
+            ((uint16_t*)m.sout)[dst[q]] = ((const uint16_t*)SA)[i];
         }
-      };
-      if (mcnt == (uint32_t)(kMaxItems * kCT) && !term_left && !term_right)  // every item of every thread
-        move(std::true_type{});
-      else
-        move(std::false_type{});
+      }
       // ---- subset offsets of the big children, at the segment starts
       // (each row holds r + 1 words below off_cap, checked when it was handed out)
       if (want_off) {
