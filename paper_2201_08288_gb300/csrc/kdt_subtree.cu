@@ -162,21 +162,23 @@ __device__ __forceinline__ uint32_t block_excl_scan_1bar(uint32_t v, uint32_t* w
 }
 
 // Weighted select by one warp with the items in registers (K per lane, cnt <=
-// 32 K): the smallest key m whose items with key <= m weigh more than
-// `rank`. Starting below the bits where every key agrees, each step counts
-// the weight of the remaining candidates whose next bit is 0 (one warp sum)
-// and fixes that bit.
+// 32 K, total weight below 2^20): the smallest key m whose items with key <= m
+// weigh more than `rank`. Starting below the bits where every key agrees, each
+// step sums, over the remaining candidates whose next bit is 0, their weight
+// and their number (one warp sum of (w << 12) | 1) and fixes that bit. The
+// answer is the key of a remaining candidate, so once a single candidate is
+// left its key is the answer and the lower bits need no steps.
 template <int K, class KeyOf, class WOf>
 __device__ __forceinline__ uint32_t warp_wsel_bits(uint32_t cnt, uint32_t rank, KeyOf key_of, WOf w_of) {
   const int lane = threadIdx.x & 31;
-  uint32_t key[K], w[K];
+  uint32_t key[K], pw[K];
   uint32_t lo = 0xffffffffu, hi = 0u;
 #pragma unroll
   for (int q = 0; q < K; ++q) {
     const uint32_t j = (uint32_t)lane + 32u * q;
     const bool ok = j < cnt;
     key[q] = ok ? key_of(j) : 0u;
-    w[q] = ok ? w_of(j) : 0u;
+    pw[q] = ok ? (w_of(j) << 12) | 1u : 0u;
     if (ok) {
       lo = min(lo, key[q]);
       hi = max(hi, key[q]);
@@ -187,15 +189,27 @@ __device__ __forceinline__ uint32_t warp_wsel_bits(uint32_t cnt, uint32_t rank, 
   if (lo >= hi) return lo;
   int bit = 31 - __clz(lo ^ hi);                    // highest bit where the keys differ
   uint32_t prefix = lo & ~((2u << bit) - 1u);       // the bits above it (none when bit = 31)
+  uint32_t ncand = cnt;                             // items matching the fixed bits
   for (; bit >= 0; --bit) {
     const uint32_t fixed = ~((1u << bit) - 1u);     // bits above `bit`, and `bit` itself
     uint32_t acc = 0;
 #pragma unroll
-    for (int q = 0; q < K; ++q) acc += ((key[q] ^ prefix) & fixed) == 0u ? w[q] : 0u;
+    for (int q = 0; q < K; ++q) acc += ((key[q] ^ prefix) & fixed) == 0u ? pw[q] : 0u;
     acc = __reduce_add_sync(0xffffffffu, acc);
-    if (rank >= acc) {
-      rank -= acc;
+    const uint32_t w0 = acc >> 12, n0 = acc & 0xfffu;
+    if (rank >= w0) {
+      rank -= w0;
       prefix |= 1u << bit;
+      ncand -= n0;
+    } else {
+      ncand = n0;
+    }
+    if (ncand == 1u) {  // the one item whose key matches the fixed bits
+      uint32_t m = 0;
+#pragma unroll
+      for (int q = 0; q < K; ++q)
+        if (pw[q] != 0u && ((key[q] ^ prefix) & fixed) == 0u) m = key[q];
+      return __reduce_max_sync(0xffffffffu, m);
     }
   }
   return prefix;
