@@ -18,7 +18,8 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 // W_NC0, W_NC1, W_ITERS (adjacent): the cell counts of the two lists and the
 // iteration count of a graph-driven run
 enum Word {
-  W_NTILES = 0, W_BIGSEG, W_HEAD, W_NEXTBIG, W_SMALL, W_BIGPTS, W_SMALLPTS, W_OFFUSED, W_MIDSEG,
+  W_NTILES = 0, W_BIGSEG, W_HEAD, W_NEXTBIG, W_BIGPTS, W_OFFUSED, W_MIDSEG,
+  W_SMALL, W_SMALLW, W_SMALLTOT, W_SMALLPTS,  // adjacent: written together by a tick
   W_NC0, W_NC1, W_ITERS, W_COUNT
 };
 // a graph-driven run's iterations (two level steps each) before it gives up
@@ -106,10 +107,13 @@ TreePlan plan_tree(const kdt_params& p0, bool no_subtree) {
   // kernel); its cells keep index order (no presort), so no leaf sort either
   const bool fourier = p.fourier_j > 0;
   t.small_max = (fourier || no_subtree) ? 0 : subtree_capacity(p.d);
+  t.sub_wide = &subtree_shape(p.d) == &kSubWide;
   t.sid_bytes = p.subset_mode == KDT_SUBSET_EXPLICIT ? (p.subset_id16 ? 2 : 1) : 0;
   const bool root_terminal = p.depth > 0 ? (n == 0) : (n <= (uint64_t)p.leaf_size);
   t.leafsort = !root_terminal && p.subset_mode != KDT_SUBSET_CONTIGUOUS && !fourier;
-  t.presorted = t.leafsort && n > (uint64_t)t.small_max;
+  // a small root is put in subset order by the subtree kernel itself, which
+  // counts at most kSubtreeHistWords subsets
+  t.presorted = t.leafsort && (n > (uint64_t)t.small_max || !subtree_sorts_root(p.r));
   t.huge_cap = t.leafsort ? n / (uint64_t)(kLeafBlockMax + 1) + 1 : 0;
   const uint64_t leaves = (uint64_t)1 << t.L_cap;
   t.maxB = std::min<uint64_t>(n / (uint64_t)(t.small_max + 1) + 1, leaves);
@@ -160,7 +164,9 @@ StepPlan plan_step(const StepNeeds& needs) {
   s.off_cap = (uint32_t)std::min<uint64_t>(needs.nseg + needs.maxB, clamp);
   s.bigseg_cap = (uint32_t)std::min<uint64_t>(needs.points / (kSelWarpMin + 1) + 1, clamp);
   const int sms = device_sms();
-  s.grid_sub = (uint32_t)(sms > 0 ? sms : 148) * (uint32_t)kSubtreeCtasPerSm;
+  s.sms = (uint32_t)(sms > 0 ? sms : 148);
+  s.grid_step = s.sms * 2u;
+  const uint32_t grid_sub_max = s.sms * (uint32_t)std::max(kSubNarrow.ctas, kSubWide.ctas);
   const uint32_t mt = std::max<uint32_t>(needs.max_trees, 1);
   size_t off = 0;
   auto take = [&](size_t b) {
@@ -190,7 +196,7 @@ StepPlan plan_step(const StepNeeds& needs) {
   s.seg_med = take((size_t)s.nseg_cap * 4);
   s.bigseg = take((size_t)s.bigseg_cap * 4);
   s.midseg = take((size_t)s.nseg_cap * 4);
-  s.slices = take((size_t)s.grid_sub * 2 * needs.slice_cells * sizeof(LCell));
+  s.slices = take((size_t)grid_sub_max * 2 * needs.slice_cells * sizeof(LCell));
   for (int b = 0; b < 2; ++b) {
     s.off[b] = take((size_t)s.off_cap * 4);
     s.obase[b] = take((size_t)s.maxB * 4);
@@ -232,6 +238,8 @@ Engine::Engine(const StepPlan& plan, uint8_t* base, cudaStream_t st) : plan_(pla
   s_.next_big_count = words_ + W_NEXTBIG;
   s_.small = small_;
   s_.small_count = words_ + W_SMALL;
+  s_.small_count_w = words_ + W_SMALLW;
+  s_.small_total = words_ + W_SMALLTOT;
   s_.small_cap = plan.cap_small;
   s_.next_big_cap = plan.maxB;
   s_.next_big_points = words_ + W_BIGPTS;
@@ -248,6 +256,7 @@ Engine::Engine(const StepPlan& plan, uint8_t* base, cudaStream_t st) : plan_(pla
   const uint32_t mt = std::max<uint32_t>(plan.needs.max_trees, 1);
   host_.assign(mt, TreeHost{});
   leafsort_.assign(mt, 0);
+  wide_.assign(mt, 0);
 }
 
 kdt_status Engine::reset() {
@@ -258,11 +267,12 @@ kdt_status Engine::reset() {
   ENGINE_TRY(cudaMemsetAsync(words_, 0, W_COUNT * 4, st_));
   ENGINE_TRY(cudaMemsetAsync(slot_words_, 0, (size_t)S_COUNT * mt * 4, st_));
   cur_ = 0;
-  big_count_ = small_count_ = 0;
+  big_count_ = small_count_ = small_count_w_ = 0;
   big_points_ = small_points_ = 0;
   root_dims_ = false;
   pending_big_.clear();
   pending_small_.clear();
+  pending_small_w_.clear();
   return KDT_OK;
 }
 
@@ -282,6 +292,7 @@ kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p
   h.max_levels = p.max_levels;
   h.fourier_j = p.fourier_j;
   h.combine_rule = p.combine_rule;
+  h.sub_wide = tp.sub_wide ? 1 : 0;
   h.stall_limit = p.key_rule == KDT_KEY_CYCLIC ? p.d : 1;
   h.sid_bytes = tp.sid_bytes;
   h.small_max = tp.small_max;
@@ -313,6 +324,7 @@ kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p
     ENGINE_TRY(cudaMemsetAsync(slot_words_ + (size_t)w * mt + slot, 0, 4, st_));
   ENGINE_TRY(cudaMemsetAsync(h.huge_count, 0, 4, st_));
   leafsort_[slot] = tp.leafsort ? 1 : 0;
+  wide_[slot] = tp.sub_wide ? 1 : 0;
   // after the build the tree's working buffers are free: the global leaf-sort
   // passes use pbuf[0] as their second buffer and xbuf[0] for tile tables
   host_[slot] = TreeHost{(uint64_t)p.n, out_perm, h.pbuf[0], (void*)h.xbuf[0], (size_t)p.d * p.n * 4};
@@ -331,8 +343,8 @@ kdt_status Engine::admit(uint32_t slot, const float* points, const kdt_params& p
   }
   const int32_t one = 1;
   ENGINE_TRY(cudaMemcpyAsync(h.live, &one, 4, cudaMemcpyHostToDevice, st_));
-  if (n <= (uint64_t)tp.small_max) {
-    pending_small_.push_back(root);
+  if (n <= (uint64_t)tp.small_max && !tp.presorted) {
+    (tp.sub_wide ? pending_small_w_ : pending_small_).push_back(root);
   } else {
     pending_big_.push_back(root);
     if (p.key_rule == KDT_KEY_WIDEST_SPREAD) root_dims_ = true;
@@ -351,16 +363,28 @@ kdt_status Engine::tick() {
     big_count_ += (uint32_t)pending_big_.size();
     pending_big_.clear();
   }
-  if (!pending_small_.empty()) {
-    if (small_count_ + pending_small_.size() > plan_.cap_small) return KDT_ERR_CAPACITY;
-    ENGINE_TRY(cudaMemcpyAsync(small_ + small_count_, pending_small_.data(),
-                               pending_small_.size() * sizeof(Cell), cudaMemcpyHostToDevice, st_));
+  if (!pending_small_.empty() || !pending_small_w_.empty()) {
+    if ((uint64_t)small_count_ + small_count_w_ + pending_small_.size() + pending_small_w_.size() > plan_.cap_small)
+      return KDT_ERR_CAPACITY;
+    if (!pending_small_.empty())
+      ENGINE_TRY(cudaMemcpyAsync(small_ + small_count_, pending_small_.data(), pending_small_.size() * sizeof(Cell),
+                                 cudaMemcpyHostToDevice, st_));
+    if (!pending_small_w_.empty()) {
+      // the back of the queue runs downwards: entry j at small[cap - 1 - j]
+      std::reverse(pending_small_w_.begin(), pending_small_w_.end());
+      const size_t m = pending_small_w_.size();
+      ENGINE_TRY(cudaMemcpyAsync(small_ + plan_.cap_small - small_count_w_ - m, pending_small_w_.data(),
+                                 m * sizeof(Cell), cudaMemcpyHostToDevice, st_));
+    }
     for (const Cell& c : pending_small_) small_points_ += c.count;
+    for (const Cell& c : pending_small_w_) small_points_ += c.count;
     small_count_ += (uint32_t)pending_small_.size();
+    small_count_w_ += (uint32_t)pending_small_w_.size();
     pending_small_.clear();
+    pending_small_w_.clear();
   }
-  const uint32_t sw[2] = {small_count_, (uint32_t)small_points_};
-  ENGINE_TRY(cudaMemcpyAsync(words_ + W_SMALL, sw, 8, cudaMemcpyHostToDevice, st_));
+  const uint32_t sw[4] = {small_count_, small_count_w_, small_count_ + small_count_w_, (uint32_t)small_points_};
+  ENGINE_TRY(cudaMemcpyAsync(words_ + W_SMALL, sw, sizeof(sw), cudaMemcpyHostToDevice, st_));
 
   if (big_count_ > 0) {
     ENGINE_TRY(cudaMemsetAsync(words_ + W_NEXTBIG, 0, 4, st_));
@@ -389,37 +413,60 @@ kdt_status Engine::tick() {
     launch_big_step(trees_, s_, tiles_bound, (uint32_t)nseg_bound, plan_.bigseg_cap, has_roots, root_dims_,
                     plan_.needs.widest, plan_.needs.max_d,
                     plan_.needs.min_d == plan_.needs.max_d ? plan_.needs.max_d : 0, tune, big_points_,
-                    plan_.grid_sub, st_, plan_.needs.fourier);
+                    plan_.grid_step, st_, plan_.needs.fourier);
     ENGINE_TRY(cudaGetLastError());
     root_dims_ = false;
-    uint32_t counts[4];
-    ENGINE_TRY(cudaMemcpyAsync(counts, words_ + W_NEXTBIG, 16, cudaMemcpyDeviceToHost, st_));
+    uint32_t w[W_COUNT];
+    ENGINE_TRY(cudaMemcpyAsync(w, words_, sizeof(w), cudaMemcpyDeviceToHost, st_));
     ENGINE_TRY(cudaStreamSynchronize(st_));
     if (debug_) {  // KDT_DEBUG=1: per-tick counts and raw tree statuses on stderr
       const uint32_t mt = std::max<uint32_t>(plan_.needs.max_trees, 1);
       std::vector<int32_t> stv(mt);
       ENGINE_TRY(cudaMemcpy(stv.data(), slot_words_ + (size_t)S_STATUS * mt, (size_t)mt * 4, cudaMemcpyDeviceToHost));
-      std::fprintf(stderr, "kdt tick: big %u -> %u, small %u\n", big_count_, counts[0], counts[1]);
+      std::fprintf(stderr, "kdt tick: big %u -> %u, small %u + %u\n", big_count_, w[W_NEXTBIG], w[W_SMALL],
+                   w[W_SMALLW]);
       for (uint32_t k = 0; k < mt; ++k)
         if (stv[k]) std::fprintf(stderr, "kdt tick: slot %u status %d\n", k, stv[k]);
     }
-    big_count_ = std::min(counts[0], plan_.maxB);
-    small_count_ = std::min(counts[1], plan_.cap_small);
-    big_points_ = counts[2];
-    small_points_ = counts[3];
+    big_count_ = std::min(w[W_NEXTBIG], plan_.maxB);
+    small_count_ = std::min(w[W_SMALL], plan_.cap_small);
+    small_count_w_ = std::min(w[W_SMALLW], plan_.cap_small - small_count_);
+    big_points_ = w[W_BIGPTS];
+    small_points_ = w[W_SMALLPTS];
     cur_ ^= 1;
   } else {
     big_count_ = 0;
     big_points_ = 0;
   }
-  if (small_count_ > 0) {
-    launch_subtree(trees_, small_, small_count_, nullptr, words_ + W_HEAD, slices_, plan_.needs.slice_cells,
-                   std::min(plan_.grid_sub, small_count_), small_points_, st_);
+  if (small_count_ > 0 || small_count_w_ > 0) {
+    launch_small(false);
     ENGINE_TRY(cudaGetLastError());
-    small_count_ = 0;
+    small_count_ = small_count_w_ = 0;
     small_points_ = 0;
   }
   return KDT_OK;
+}
+
+void Engine::launch_small(bool from_device) {
+  const uint32_t cap = plan_.cap_small;
+  const uint32_t gn = plan_.sms * (uint32_t)kSubNarrow.ctas, gw = plan_.sms * (uint32_t)kSubWide.ctas;
+  if (from_device) {
+    // counts on the device (a recorded tick): the narrow front, then the wide
+    // back walked from the end
+    launch_subtree(kSubNarrow, trees_, small_, cap, words_ + W_SMALL, false, words_ + W_HEAD, slices_,
+                   plan_.needs.slice_cells, gn, 0, st_);
+    launch_subtree(kSubWide, trees_, small_, cap, words_ + W_SMALLW, true, words_ + W_HEAD, slices_,
+                   plan_.needs.slice_cells, gw, 0, st_);
+    return;
+  }
+  const uint64_t pts = small_points_;
+  if (small_count_ > 0)
+    launch_subtree(kSubNarrow, trees_, small_, small_count_, nullptr, false, words_ + W_HEAD, slices_,
+                   plan_.needs.slice_cells, std::min(gn, small_count_), pts, st_);  // the points of both
+  if (small_count_w_ > 0)
+    launch_subtree(kSubWide, trees_, small_ + cap - small_count_w_, small_count_w_, nullptr, false,
+                   words_ + W_HEAD, slices_, plan_.needs.slice_cells, std::min(gw, small_count_w_),
+                   small_count_ ? 0 : pts, st_);
 }
 
 kdt_status Engine::done_slots(const std::vector<uint32_t>& slots, std::vector<uint32_t>* done) {
@@ -504,8 +551,7 @@ kdt_status Engine::record_tick(int p) {
   ENGINE_TRY(cudaMemsetAsync(words_ + W_NC0 + (p ^ 1), 0, 4, st_));
   ENGINE_TRY(cudaMemsetAsync(words_ + W_BIGPTS, 0, 4, st_));
   ENGINE_TRY(cudaMemsetAsync(words_ + W_OFFUSED, 0, 4, st_));
-  ENGINE_TRY(cudaMemsetAsync(words_ + W_SMALL, 0, 4, st_));
-  ENGINE_TRY(cudaMemsetAsync(words_ + W_SMALLPTS, 0, 4, st_));
+  ENGINE_TRY(cudaMemsetAsync(words_ + W_SMALL, 0, 4 * (W_SMALLPTS - W_SMALL + 1), st_));
   StepDev sd = s_;
   sd.cells = big_[p];
   sd.ncells = plan_.maxB;  // a capacity: the count is the device word
@@ -522,17 +568,16 @@ kdt_status Engine::record_tick(int p) {
   sd.warp_max = tune.warp_max;
   launch_big_step(trees_, sd, plan_.max_tiles, plan_.nseg_cap, plan_.bigseg_cap, false, false, plan_.needs.widest,
                   plan_.needs.max_d, plan_.needs.min_d == plan_.needs.max_d ? plan_.needs.max_d : 0, tune, 0,
-                  plan_.grid_sub, st_, plan_.needs.fourier);
+                  plan_.grid_step, st_, plan_.needs.fourier);
   ENGINE_TRY(cudaGetLastError());
-  launch_subtree(trees_, small_, plan_.cap_small, words_ + W_SMALL, words_ + W_HEAD, slices_,
-                 plan_.needs.slice_cells, plan_.grid_sub, 0, st_);
+  launch_small(true);
   ENGINE_TRY(cudaGetLastError());
   return KDT_OK;
 }
 
 kdt_status Engine::run_graph() {
   // the roots' step (presort, root dims) is sized and launched by the host
-  if (!pending_big_.empty() || !pending_small_.empty()) {
+  if (!pending_big_.empty() || !pending_small_.empty() || !pending_small_w_.empty()) {
     const kdt_status s = tick();
     if (s != KDT_OK) return s;
   }
@@ -602,13 +647,14 @@ kdt_status Engine::run_graph() {
   if (fin[2] > 1) trace_add_launches((uint64_t)(fin[2] - 1) * per_iter);  // replays beyond the recorded one
   graph_iters_ = fin[2];
   if (fin[p0] != 0) return KDT_ERR_CUDA;  // stopped at the iteration cap with cells left
-  big_count_ = small_count_ = 0;
+  big_count_ = small_count_ = small_count_w_ = 0;
   big_points_ = small_points_ = 0;
   return KDT_OK;
 }
 
 kdt_status Engine::run_to_completion() {
-  for (int guard = 0; busy() || !pending_big_.empty() || !pending_small_.empty(); ++guard) {
+  for (int guard = 0; busy() || !pending_big_.empty() || !pending_small_.empty() || !pending_small_w_.empty();
+       ++guard) {
     if (guard > 2 * KDT_MAX_LEVELS + 4) return KDT_ERR_CUDA;
     const kdt_status s = tick();
     if (s != KDT_OK) return s;

@@ -29,7 +29,8 @@ struct TreePlan {
   int L_cap = 0;
   int small_max = 0;
   int sid_bytes = 0;
-  bool presorted = false;  // big root and subsets not already in index order
+  bool sub_wide = false;   // small cells run in the subtree kernel's wide shape
+  bool presorted = false;  // root split by the pipeline, reordered by subset first
   bool leafsort = false;   // subsets not in index order: leaves are sorted at the end
   uint64_t n = 0;
   uint64_t term_cap = 0;
@@ -57,7 +58,9 @@ struct StepNeeds {
 
 struct StepPlan {
   StepNeeds needs;
-  uint32_t maxB = 0, cap_small = 0, max_tiles = 0, nseg_cap = 0, bigseg_cap = 0, grid_sub = 0, off_cap = 0;
+  // grid_step: the grid scale of the level step's kernels (two per SM);
+  // sms: the device's SMs (the subtree kernel's grid is sms x its shape's CTAs)
+  uint32_t maxB = 0, cap_small = 0, max_tiles = 0, nseg_cap = 0, bigseg_cap = 0, grid_step = 0, sms = 0, off_cap = 0;
   size_t trees = 0, words = 0, slot_words = 0, slots_list = 0, big[2] = {0, 0}, small = 0, tile_base = 0,
          seg_base = 0, tiles = 0, tile_left = 0, tile_loff = 0, tile_mm = 0, child_mm = 0, kdim = 0,
          mkey = 0, lcount = 0, seg_w = 0, seg_key = 0, seg_med = 0, bigseg = 0, midseg = 0, slices = 0,
@@ -87,7 +90,7 @@ class Engine {
   // One tick (see above). Synchronises the stream once.
   kdt_status tick();
   // True while some cell of some tree still waits for a tick.
-  bool busy() const { return big_count_ > 0 || small_count_ > 0; }
+  bool busy() const { return big_count_ > 0 || small_count_ > 0 || small_count_w_ > 0; }
   // Slots (among `slots`) whose trees have no cell left.
   kdt_status done_slots(const std::vector<uint32_t>& slots, std::vector<uint32_t>* done);
   // Offsets and sentinels of finished trees, then their status and L.
@@ -117,16 +120,20 @@ class Engine {
   LCell* slices_ = nullptr;
   StepDev s_{};
   int cur_ = 0;
-  uint32_t big_count_ = 0, small_count_ = 0;
+  uint32_t big_count_ = 0, small_count_ = 0, small_count_w_ = 0;  // small: front (narrow), back (wide)
   uint64_t big_points_ = 0, small_points_ = 0;
   bool root_dims_ = false;
   bool debug_ = false;
   uint32_t graph_iters_ = 0;
   // Record a tick over cell list p into the stream's capture (counts on the device).
   kdt_status record_tick(int p);
-  std::vector<Cell> pending_big_, pending_small_;
+  // The subtree kernel over the small-cell queue: the narrow shape over its
+  // front, the wide one over its back (host counts, or the device's).
+  void launch_small(bool from_device);
+  std::vector<Cell> pending_big_, pending_small_, pending_small_w_;
   std::vector<TreeHost> host_;       // per slot: leaf-sort view of a presorted tree
   std::vector<uint8_t> leafsort_;    // per slot
+  std::vector<uint8_t> wide_;        // per slot: the tree's small cells use the wide shape
 };
 
 }  // namespace kdt

@@ -80,7 +80,7 @@ struct TreeDev {
   uint32_t huge_cap;
   int32_t fourier_j;     // > 0: splits by the Fourier-moment estimator with this many harmonics
   int32_t combine_rule;  // 0: count-weighted median of the subset medians; 1: every subset counts once
-  int32_t pad0;
+  int32_t sub_wide;      // small cells run in the subtree kernel's wide shape (else the narrow one)
   uint32_t* out_perm;
   float* out_vals;
   int8_t* out_dims;
@@ -143,8 +143,11 @@ struct StepDev {
   uint32_t* tile_loff;    // [ntiles]
   Cell* next_big;         // children that stay in the multi-CTA pipeline
   uint32_t* next_big_count;
-  Cell* small;            // children that finish in the subtree kernel
-  uint32_t* small_count;
+  Cell* small;            // children that finish in the subtree kernel: cells of narrow-shape
+                          // trees from the front, of wide-shape trees from the back
+  uint32_t* small_count;  // cells at the front
+  uint32_t* small_count_w;  // cells at the back (small[small_cap - 1 - j])
+  uint32_t* small_total;    // both (appends past small_cap fail)
   uint32_t next_big_cap;
   uint32_t small_cap;
   uint32_t* next_big_points;  // points in next_big (for bandwidth accounting)

@@ -10,8 +10,8 @@
 
 namespace kdt {
 
-// Per-level local cell of the subtree kernel (shared memory while a level has
-// at most kSubtreeSmemCells live cells, else a per-CTA slice of global memory).
+// Per-level local cell of the subtree kernel (shared memory while a level's
+// live cells fit the shape's table, else a per-CTA slice of global memory).
 struct LCell {
   uint32_t heap;
   uint32_t mkey;    // split key
@@ -23,42 +23,64 @@ struct LCell {
 };
 static_assert(sizeof(LCell) == 16, "LCell is 16 bytes");
 
-// Shared-memory budget of the subtree kernel: kSubtreeCtasPerSm CTAs share an
-// SM, each finishing its own cell, so that one CTA's barriers and copies
-// overlap the other's work.
-constexpr int kSubtreeCtasPerSm = 2;
-constexpr size_t kSubtreeSmemBytes = 112 * 1024;  // dynamic part, per CTA
-constexpr int kSubtreeBigCap = 1024;              // segments above the rank-counting size
-constexpr int kSubtreeSmemCells = 256;
-constexpr int kSubtreeMaxPoints = 2048;           // a cell the kernel takes: at most 8 points per thread
-constexpr size_t kSubtreeFixedBytes = (size_t)kSubtreeWarps * 256 * 4 /* warp histograms */ +
-                                      (size_t)kSubtreeBigCap * 2 + 2 * (size_t)kSubtreeSmemCells * sizeof(LCell);
+// The subtree kernel comes in two shapes (kSubtreeThreads threads per CTA in
+// both); each tree uses one, by its coordinate count:
+//   narrow (d <= kSubtreeNarrowMaxD): at most 5 positions per thread (1280
+//     points), three CTAs per SM in 74 KB of dynamic shared memory each, cell
+//     tables of 128 cells;
+//   wide (larger d): at most 8 positions per thread (2048 points), two CTAs
+//     per SM in 112 KB each, cell tables of 256 cells.
+// Several CTAs share an SM, each finishing its own cell, so that one CTA's
+// barriers and copies overlap the others' work.
+struct SubtreeShape {
+  int q;        // positions per thread
+  int ctas;     // CTAs per SM
+  size_t smem;  // dynamic shared memory per CTA
+  int cells;    // cells of one level's table in shared memory
+};
+constexpr SubtreeShape kSubNarrow{5, 3, 74 * 1024, 128};
+constexpr SubtreeShape kSubWide{8, 2, 112 * 1024, 256};
+constexpr int kSubtreeNarrowMaxD = 8;
+constexpr int kSubtreeBigCap = 64;           // segments above the rank-counting size (32): N / 33 < 64
+constexpr int kSubtreeHistWords = kSubtreeWarps * 256;  // warp histograms; also the root's subset counts
+__host__ __device__ constexpr size_t subtree_fixed_bytes(int cells) {
+  return (size_t)kSubtreeHistWords * 4 + (size_t)kSubtreeBigCap * 2 + 2 * (size_t)cells * sizeof(LCell);
+}
+inline const SubtreeShape& subtree_shape(int d) { return d <= kSubtreeNarrowMaxD ? kSubNarrow : kSubWide; }
 
 // Column stride (elements) of a cell of N points in shared memory: room for
 // the 16-byte alignment phase of the bulk copies.
 __host__ __device__ inline uint32_t subtree_stride(uint32_t N) { return (N + 8 + 3) & ~3u; }
 
 // Bytes of shared memory a cell of N points with d coordinates needs beyond
-// the fixed part: d key columns and the permutation at the padded stride, the
-// keys in local order and the segment medians (4 bytes each), the subset ids,
-// two orders, cell ids, a scan, the segment starts and a flag array (2 bytes
-// each).
+// the fixed part: d key columns at the padded stride, the keys in local order
+// and the segment medians (4 bytes each), the subset ids, two orders, cell
+// ids, a scan and the segment starts (2 bytes each).
 __host__ __device__ inline size_t subtree_point_bytes(uint32_t N, int d) {
   const size_t stride = subtree_stride(N);
-  return (size_t)(d + 1) * stride * 4 + 2 * (((size_t)N * 4 + 15) & ~(size_t)15) +
-         7 * ((((size_t)N + 1) * 2 + 15) & ~(size_t)15);
+  return (size_t)d * stride * 4 + 2 * (((size_t)N * 4 + 15) & ~(size_t)15) +
+         6 * ((((size_t)N + 1) * 2 + 15) & ~(size_t)15);
 }
 
-// Largest cell (points) the subtree kernel holds for d coordinates.
+// Largest cell (points) the subtree kernel holds for d coordinates in the
+// shape that trees of d coordinates use.
 inline int subtree_capacity(int d) {
+  if (d < 1) return 0;
+  const SubtreeShape& sh = subtree_shape(d);
+  const size_t fixed = subtree_fixed_bytes(sh.cells);
   int lo = 32, hi = 8192;
-  if (kSubtreeFixedBytes + subtree_point_bytes(lo, d) > kSubtreeSmemBytes) return 0;
+  if (fixed + subtree_point_bytes(lo, d) > sh.smem) return 0;
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
-    if (kSubtreeFixedBytes + subtree_point_bytes(mid, d) <= kSubtreeSmemBytes) lo = mid; else hi = mid - 1;
+    if (fixed + subtree_point_bytes(mid, d) <= sh.smem) lo = mid; else hi = mid - 1;
   }
-  return std::min(lo & ~31, kSubtreeMaxPoints);
+  return std::min(lo & ~31, sh.q * kSubtreeThreads);
 }
+
+// Subset counts of a small root (put in subset order by the subtree kernel)
+// live in the warp histograms: trees with more subsets presort their root in
+// the multi-CTA pipeline instead.
+inline bool subtree_sorts_root(int r) { return r <= kSubtreeHistWords; }
 
 // The tuning of the select paths (kdt_tuning, validated) in force when a level
 // step starts.
@@ -93,11 +115,13 @@ void launch_shard_medians(const TreeDev* trees, const StepDev& s, uint32_t ncell
 void launch_shard_minmax(const TreeDev* trees, const StepDev& s, uint32_t ncells_cap, cudaStream_t st);
 
 cudaError_t prepare_subtree_kernel();
-// count_dev: if set, the device word holding the queue's length (count is
-// then its cap)
-void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t* count_dev,
-                    uint32_t* head, LCell* slices, uint32_t slice_cells, uint32_t grid, uint64_t points,
-                    cudaStream_t st);
+// One launch of the subtree kernel in the given shape over a queue of small
+// cells. count_dev: if set, the device word holding the queue's length
+// (count is then its cap). reversed: the queue is filled from the end of the
+// list (item j at list[count_cap - 1 - j], count_cap = count).
+void launch_subtree(const SubtreeShape& sh, const TreeDev* trees, const Cell* list, uint32_t count,
+                    const uint32_t* count_dev, bool reversed, uint32_t* head, LCell* slices, uint32_t slice_cells,
+                    uint32_t grid, uint64_t points, cudaStream_t st);
 
 void launch_iota(uint32_t* out, uint32_t n, cudaStream_t st);
 

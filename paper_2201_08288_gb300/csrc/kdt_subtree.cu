@@ -3,7 +3,7 @@
 //
 // A cell with at most subtree_capacity(d) points is staged once into shared
 // memory with bulk asynchronous copies (cp.async.bulk, completion on an
-// mbarrier): all d coordinate columns and the permutation. Its points are in
+// mbarrier): all d coordinate columns. Its points are in
 // subset order (the layout invariant of kdt_internal.cuh; the root of a small
 // tree is put in that order here by a counting sort), and the local order is
 // kept by stable partitions, so every (cell, subset) segment is a contiguous
@@ -20,8 +20,10 @@
 //   4. per cell, the count-weighted lower median of its segments' medians;
 //   5. a stable partition of the local order around the split (ties left);
 //   6. children: terminal cells are recorded, the others form the next level.
-// The permutation is written once, at the end. The kernel is persistent: each
-// CTA pulls cells from a queue.
+// The permutation is written once, at the end, gathered from the cell's
+// incoming permutation in global memory. The kernel is persistent: each CTA
+// pulls cells from a queue. It is compiled for the two shapes of
+// kdt_launch.h (positions per thread, CTAs per SM, cell-table size).
 #include <algorithm>
 #include <type_traits>
 
@@ -38,25 +40,22 @@ constexpr int T = kSubtreeThreads;
 constexpr int NW = kSubtreeWarps;
 constexpr uint16_t kNoCell = 0xffff;
 constexpr uint32_t kRankMax = 32;
-constexpr int kQ = kSubtreeMaxPoints / T;  // positions per thread
-static_assert(kQ * NW == 64, "the block counts of a level fill two words per lane");
 
 // -------------------------------------------------------- shared layout
 
 struct Smem {
   uint32_t* whist;    // NW * 256 words: warp histograms, tables of few cells, root subset counts
   uint16_t* biglist;  // kSubtreeBigCap segments above kRankMax points
-  LCell* tab;        // 2 * kSubtreeSmemCells: the cell tables of two levels
-  uint32_t* cols;     // (d + 1) columns at stride `stride`; column d is the permutation
+  LCell* tab;         // 2 * cells: the cell tables of two levels
+  uint32_t* cols;     // d key columns at stride `stride`
   uint32_t* gk;       // N: key of each position on its cell's coordinate
   uint32_t* smed;     // N: median of each segment
   uint16_t* sid;      // N: subset of each local point
   uint16_t* ordA;     // N: local point at each position
   uint16_t* ordB;     // N
   uint16_t* cellid;   // N: live cell of each position (kNoCell: finished)
-  uint16_t* pre;      // N + 1: exclusive prefix of `aux`
+  uint16_t* pre;      // N + 1: exclusive prefix of the segment starts, then of the left flags
   uint16_t* segs;     // N + 1: first position of each segment
-  uint16_t* aux;      // N: segment-start flag, then left flag
 };
 
 __device__ __forceinline__ uint32_t al16(uint32_t off) { return (off + 15u) & ~15u; }
@@ -64,7 +63,7 @@ __device__ __forceinline__ uint32_t al16(uint32_t off) { return (off + 15u) & ~1
 // Carve the dynamic shared memory with plain byte offsets from its base (no
 // pointer is stored through another pointer), so that the compiler keeps
 // every array in the shared address space.
-__device__ __forceinline__ Smem carve(uint8_t* base, uint32_t N, int d) {
+__device__ __forceinline__ Smem carve(uint8_t* base, uint32_t N, int d, int cells) {
   Smem s;
   uint32_t off = 0;
   s.whist = (uint32_t*)(base + off);
@@ -72,9 +71,9 @@ __device__ __forceinline__ Smem carve(uint8_t* base, uint32_t N, int d) {
   s.biglist = (uint16_t*)(base + off);
   off += (uint32_t)kSubtreeBigCap * 2u;
   s.tab = (LCell*)(base + off);
-  off += 2u * (uint32_t)kSubtreeSmemCells * (uint32_t)sizeof(LCell);
+  off += 2u * (uint32_t)cells * (uint32_t)sizeof(LCell);
   s.cols = (uint32_t*)(base + off);
-  off += (uint32_t)(d + 1) * subtree_stride(N) * 4u;
+  off += (uint32_t)d * subtree_stride(N) * 4u;
   s.gk = (uint32_t*)(base + off);
   off = al16(off + N * 4u);
   s.smed = (uint32_t*)(base + off);
@@ -91,8 +90,6 @@ __device__ __forceinline__ Smem carve(uint8_t* base, uint32_t N, int d) {
   s.pre = (uint16_t*)(base + off);
   off = al16(off + a);
   s.segs = (uint16_t*)(base + off);
-  off = al16(off + a);
-  s.aux = (uint16_t*)(base + off);
   return s;
 }
 
@@ -126,10 +123,13 @@ __device__ __forceinline__ int warp_pick_widest(const uint32_t (&lo)[2], const u
 
 // Exclusive prefix, over all positions, of the flags whose warp ballots are
 // bal[q] (position tid + q T, block q NW + warp), given the popcount of every
-// block in cnt[64] (block order = position order); *total is the sum.
+// block in cnt[kQ NW] (block order = position order; at most 64 blocks);
+// *total is the sum.
+template <int kQ>
 __device__ __forceinline__ void block_counts_scan(const unsigned (&bal)[kQ], const uint32_t* cnt, int lane,
                                                   int warp, uint32_t (&excl)[kQ], uint32_t* total) {
-  const uint32_t c0 = cnt[lane], c1 = cnt[lane + 32];
+  static_assert(kQ * NW <= 64, "two block counts per lane at most");
+  const uint32_t c0 = lane < kQ * NW ? cnt[lane] : 0u, c1 = lane + 32 < kQ * NW ? cnt[lane + 32] : 0u;
   const uint32_t i0 = warp_incl_scan(c0);
   const uint32_t i1 = warp_incl_scan(c1) + __shfl_sync(0xffffffffu, i0, 31);
   *total = __shfl_sync(0xffffffffu, i1, 31);
@@ -215,15 +215,20 @@ __device__ __forceinline__ uint32_t warp_wsel_bits(uint32_t cnt, uint32_t rank, 
   return prefix;
 }
 
-__global__ void __launch_bounds__(T, kSubtreeCtasPerSm)
-k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t* count_dev, uint32_t* head,
-          LCell* slices, uint32_t slice_cells, uint32_t probe_tries) {
+// kWide: compiled for the wide shape, else the narrow one (kdt_launch.h).
+template <bool kWide>
+__global__ void __launch_bounds__(T, (kWide ? kSubWide : kSubNarrow).ctas)
+k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t* count_dev, uint32_t reversed,
+          uint32_t* head, LCell* slices, uint32_t slice_cells, uint32_t probe_tries) {
+  constexpr SubtreeShape kSh = kWide ? kSubWide : kSubNarrow;
+  constexpr int kQ = kSh.q, kCells = kSh.cells;
   extern __shared__ __align__(128) uint8_t smem_raw[];
+  const uint32_t count_cap = count;
   if (count_dev) count = min(*count_dev, count);  // a graph-driven step: the queue's length, capped
   __shared__ uint32_t tmp[33];
   __shared__ uint32_t s_item, s_ncur, s_nbig, s_where, s_fail;
   __shared__ __align__(8) uint64_t s_bar;
-  __shared__ uint32_t s_colbase[kMaxDims + 1];
+  __shared__ uint32_t s_colbase[kMaxDims];
   __shared__ uint32_t s_bcnt[kQ * NW];  // per-block counts of a level's position flags
   __shared__ uint32_t s_wtot[NW];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -245,7 +250,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
     __syncthreads();
     const uint32_t item = s_item;
     if (item >= count) break;
-    const Cell c = list[item];
+    const Cell c = list[reversed ? count_cap - 1u - item : item];
     const TreeDev& t = trees[c.tree];
     if (probe_tries && tid == 0) {
       // injected fault (kdt_fault_inject): wait on a phase that nothing
@@ -272,26 +277,32 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
     const uint32_t N = c.count;
     const int d = t.d, r = t.r;
     const int64_t n = t.n;
+    if (N > (uint32_t)(kQ * T) || subtree_fixed_bytes(kCells) + subtree_point_bytes(N, d) > kSh.smem) {
+      // a queue holds only cells within its shape's capacity
+      if (tid == 0) {
+        set_status(t, ST_INTERNAL);
+        atomicSub(t.live, 1);
+      }
+      continue;
+    }
     const uint32_t stride = subtree_stride(N);
-    Smem S = carve(smem_raw, N, d);
-    // Column l of the cell sits at S.cols + s_colbase[l]; column d holds the
-    // permutation. Each column's offset absorbs the 16-byte alignment phase
-    // of its global source so that the bulk copies are aligned on both sides.
+    Smem S = carve(smem_raw, N, d, kCells);
+    // Column l of the cell sits at S.cols + s_colbase[l]. Each column's
+    // offset absorbs the 16-byte alignment phase of its global source so that
+    // the bulk copies are aligned on both sides.
+    const uint32_t* P = src_perm(t, c.level);  // incoming permutation (null: the identity)
 
     // ---- 0. stage the cell: bulk copies of the aligned middle, plain loads at the edges
     {
       const float* X = src_cols(t, c.level);
-      const uint32_t* P = src_perm(t, c.level);
       const uint32_t b0 = c.begin, e0 = c.begin + N;
-      const int ncols = d + (P ? 1 : 0);
-      auto src_of = [&](int l) -> const uint32_t* {
-        return l < d ? (const uint32_t*)(X + (int64_t)l * n) : P;
-      };
+      const int ncols = d;
+      auto src_of = [&](int l) -> const uint32_t* { return (const uint32_t*)(X + (int64_t)l * n); };
       // phase of element b0 of column l: elements past the previous 16-byte boundary
       auto phase_of = [&](int l) -> uint32_t {
         return (uint32_t)(((uintptr_t)(src_of(l) + b0) >> 2) & 3u);
       };
-      if (tid <= d) s_colbase[tid] = (uint32_t)tid * stride + (tid < ncols ? phase_of(tid) : 0u);
+      if (tid < d) s_colbase[tid] = (uint32_t)tid * stride + phase_of(tid);
       if (tid == 0) {
         uint32_t total = 0;
         for (int l = 0; l < ncols; ++l) {
@@ -319,9 +330,6 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
         if (ok) S.cols[(size_t)l * stride + ph + (idx - b0)] = src_of(l)[idx];
       }
       __syncthreads();
-      uint32_t* pm0 = S.cols + s_colbase[d];
-      if (!P)
-        for (uint32_t i = tid; i < N; i += T) pm0[i] = b0 + i;
       // explicit subset ids are read from global memory while the bulk copies
       // run (neither touches the other's shared memory), eight loads in
       // flight per thread
@@ -383,7 +391,8 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
       }
       if (nan) set_status(t, ST_NAN_INPUT);
       if (!expl)
-        for (uint32_t i = tid; i < N; i += T) S.sid[i] = (uint16_t)subset_of(t, SID, pm0[i], (int64_t)b0 + i);
+        for (uint32_t i = tid; i < N; i += T)
+          S.sid[i] = (uint16_t)subset_of(t, SID, P ? P[b0 + i] : b0 + i, (int64_t)b0 + i);
       // The root of a small tree arrives in index order: put it in subset
       // order (counting sort; order inside a subset is immaterial). Every
       // other cell is in subset order already.
@@ -415,7 +424,6 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
     }
     __syncthreads();
 
-    const uint32_t* pm = S.cols + s_colbase[d];
     uint16_t* ordA = S.ordA;
     uint16_t* ordB = S.ordB;
     int which = 0;
@@ -428,7 +436,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
       // that outgrew it and lives in this CTA's global slice.
       auto level_body = [&](auto in_global) {
         LCell* cc = decltype(in_global)::value ? gslice + (size_t)which * slice_cells
-                                               : S.tab + which * kSubtreeSmemCells;
+                                               : S.tab + which * kCells;
 
         // ---- 1. key coordinate of every live cell
         if (t.key_rule == KEY_CYCLIC) {
@@ -723,8 +731,8 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
           }
           const uint32_t nlive = (uint32_t)live[0] + (uint32_t)live[1];
           const uint32_t ex = block_excl_scan_1bar(nlive, s_wtot, lane, warp, &run_out);
-          nwhere = run_out <= (uint32_t)kSubtreeSmemCells ? 0 : 1;
-          LCell* nc = nwhere ? gslice + (size_t)(which ^ 1) * slice_cells : S.tab + (which ^ 1) * kSubtreeSmemCells;
+          nwhere = run_out <= (uint32_t)kCells ? 0 : 1;
+          LCell* nc = nwhere ? gslice + (size_t)(which ^ 1) * slice_cells : S.tab + (which ^ 1) * kCells;
           if (k < ncur) {
             const uint32_t li = live[0] ? ex : kNoCell;
             const uint32_t ri = live[1] ? ex + (live[0] ? 1u : 0u) : kNoCell;
@@ -746,8 +754,8 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
             }
             block_excl_scan(sum, tmp, &total_live);
           }
-          nwhere = total_live <= (uint32_t)kSubtreeSmemCells ? 0 : 1;
-          LCell* nc = nwhere ? gslice + (size_t)(which ^ 1) * slice_cells : S.tab + (which ^ 1) * kSubtreeSmemCells;
+          nwhere = total_live <= (uint32_t)kCells ? 0 : 1;
+          LCell* nc = nwhere ? gslice + (size_t)(which ^ 1) * slice_cells : S.tab + (which ^ 1) * kCells;
           for (uint32_t k0 = 0; k0 < ncur; k0 += T) {
             const uint32_t k = k0 + tid;
             LCell ch[2] = {};
@@ -808,7 +816,10 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
     }
 
     // ---- write the permutation in final order
-    for (uint32_t i = tid; i < N; i += T) t.out_perm[(int64_t)c.begin + i] = pm[ordA[i]];
+    for (uint32_t i = tid; i < N; i += T) {
+      const uint32_t o = c.begin + ordA[i];
+      t.out_perm[(int64_t)c.begin + i] = P ? P[o] : o;
+    }
     if (tid == 0) atomicSub(t.live, 1);
   }
 }
@@ -884,19 +895,31 @@ void launch_iota(uint32_t* out, uint32_t n, cudaStream_t st) {
   k_iota<<<std::min<uint32_t>((n + 255) / 256, 4096u), 256, 0, st>>>(out, n);
 }
 
-cudaError_t prepare_subtree_kernel() {
-  return cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kSubtreeSmemBytes);
+// The kernel instance of a shape.
+using SubtreeKernel = void (*)(const TreeDev*, const Cell*, uint32_t, const uint32_t*, uint32_t, uint32_t*, LCell*,
+                               uint32_t, uint32_t);
+SubtreeKernel subtree_kernel(const SubtreeShape& sh) {
+  return sh.q == kSubWide.q ? k_subtree<true> : k_subtree<false>;
 }
 
-void launch_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t* count_dev,
-                    uint32_t* head, LCell* slices, uint32_t slice_cells, uint32_t grid, uint64_t points,
-                    cudaStream_t st) {
-  if (count == 0) return;
+cudaError_t prepare_subtree_kernel() {
+  for (const SubtreeShape* sh : {&kSubNarrow, &kSubWide}) {
+    const cudaError_t e = cudaFuncSetAttribute(subtree_kernel(*sh), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sh->smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+void launch_subtree(const SubtreeShape& sh, const TreeDev* trees, const Cell* list, uint32_t count,
+                    const uint32_t* count_dev, bool reversed, uint32_t* head, LCell* slices, uint32_t slice_cells,
+                    uint32_t grid, uint64_t points, cudaStream_t st) {
+  if (count == 0 || grid == 0) return;
   cudaMemsetAsync(head, 0, sizeof(uint32_t), st);
   const uint32_t probe = fault_take(KDT_FAULT_WAIT) ? 1024u : 0u;
   TraceScope ts(K_SUBTREE, st, points);
-  k_subtree<<<grid, T, kSubtreeSmemBytes, st>>>(trees, list, count, count_dev, head, slices, slice_cells, probe);
+  subtree_kernel(sh)<<<grid, T, sh.smem, st>>>(trees, list, count, count_dev, reversed ? 1u : 0u, head, slices,
+                                               slice_cells, probe);
 }
 
 void launch_finalize_many(const TreeDev* trees, const uint32_t* slots, uint32_t nslots, uint32_t max_records,

@@ -97,17 +97,17 @@ def test_dims_around_subtree_capacity(d):
 
 
 def test_big_steps_with_many_cells():
-    """d = 16 (subtree capacity 1056) and cells of about 1100 points at level
-    10: more than a thousand big cells in one step, where the combine and the
-    tile scan run a warp per cell."""
+    """d = 16 and cells of about 48 points more than the subtree capacity at
+    level 10: more than a thousand big cells in one step, where the combine
+    and the tile scan run a warp per cell."""
     from paper_2201_08288_gb300 import kdt
-    assert kdt.kdt_subtree_capacity(16) < 1100
-    n, d = 1024 * 1100, 16
+    d = 16
+    n = 1024 * (kdt.kdt_subtree_capacity(d) + 48)
     pts = np.random.default_rng(11).standard_normal((d, n)).astype(np.float32)
     check_against_oracle(pts, r=8, subset_mode=0, depth=11, key_rule=1)
 
 
-@pytest.mark.parametrize("d", [1, 3])
+@pytest.mark.parametrize("d", [1, 3, 16])
 def test_subtree_levels_with_many_live_cells(d):
     """One cell of the subtree kernel's full capacity split down to single
     points: its deep levels hold more live cells than the kernel's
@@ -143,6 +143,20 @@ def test_singleton_subsets_exact_median():
     g = check_against_oracle(pts, sid=sid, r=n, subset_mode=2, depth=9)
     ref1 = oracle.build_tree(pts, r=1, depth=9)
     np.testing.assert_array_equal(g.perm, ref1.perm)
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_small_roots_with_more_subsets_than_the_root_sort_counts(mode):
+    """Roots within the subtree capacity whose r exceeds the subset counts the
+    subtree kernel keeps for a root (2048): the pipeline puts them in subset
+    order and splits them first."""
+    from paper_2201_08288_gb300 import kdt
+    rng = np.random.default_rng(70 + mode)
+    n = kdt.kdt_subtree_capacity(3) - 100
+    pts = rng.standard_normal((3, n)).astype(np.float32)
+    sid = rng.integers(0, 3000, n).astype(np.uint16) if mode == 2 else None
+    check_against_oracle(pts, sid=sid, r=3000, subset_mode=mode, depth=7)
+    check_against_oracle(pts, sid=sid, r=3000, subset_mode=mode, depth=0, leaf_size=5, max_levels=20, key_rule=1)
 
 
 def test_max_subsets_large_cells():

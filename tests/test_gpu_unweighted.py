@@ -47,7 +47,7 @@ def test_unweighted_rule_matches_oracle(case):
         pts = rng.integers(-8, 9, (2, 60000)).astype(np.float32) / 4
         kw = dict(r=7, subset_mode=0, depth=0, leaf_size=24, max_levels=24)
     elif case == 4:  # a small tree: subtree kernel only
-        pts = workloads.uniform(1500, 4, seed=64)
+        pts = workloads.uniform(1200, 4, seed=64)
         kw = dict(r=9, subset_mode=0, depth=7, key_rule=1)
     else:  # singleton subsets: the exact lower median either way
         pts = workloads.uniform(3000, 2, seed=65)
