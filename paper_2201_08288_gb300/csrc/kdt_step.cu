@@ -1344,8 +1344,10 @@ __device__ __forceinline__ void classify_cell(const TreeDev* trees, const StepDe
       ++live_delta;
       const Cell child{cb[side], cc[side], heap, cell.tree, (int8_t)level, (int8_t)stall, (int16_t)-1};
       if (cc[side] <= (uint32_t)t.small_max) {
-        const uint32_t slot = atomicAdd(s.small_count, 1u);
-        if (slot < s.small_cap) {
+        if (atomicAdd(s.small_total, 1u) < s.small_cap) {
+          // the two ends of the queue never meet: at most small_cap cells get a slot
+          const uint32_t slot = t.sub_wide ? s.small_cap - 1u - atomicAdd(s.small_count_w, 1u)
+                                           : atomicAdd(s.small_count, 1u);
           s.small[slot] = child;
           cr = make_uint2(kNoRow, slot);  // its widest coordinate is picked with the big children's
         } else {
