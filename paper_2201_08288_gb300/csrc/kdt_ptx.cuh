@@ -94,6 +94,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Prefetch of a global range into L2 by the bulk-copy engine (16-byte
+// aligned address, size a multiple of 16; no completion to wait for).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Bulk copy shared -> global in the current bulk group (16-byte aligned
 // addresses, size a multiple of 16).
 __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {

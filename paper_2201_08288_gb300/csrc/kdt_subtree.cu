@@ -319,6 +319,13 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
           if (a1 > a0)
             bulk_g2s(S.cols + (size_t)l * stride + ph + (a0 - b0), src_of(l) + a0, (a1 - a0) * 4u, &s_bar);
         }
+        if (P) {
+          // the incoming permutation is gathered at the end: bring the cell's
+          // range into L2 now (whole 16-byte blocks; buffers are 256-byte
+          // aligned and padded to a multiple of 256 bytes)
+          const uintptr_t p0 = (uintptr_t)(P + b0) & ~(uintptr_t)15, p1 = ((uintptr_t)(P + e0) + 15) & ~(uintptr_t)15;
+          bulk_prefetch_l2((const void*)p0, (uint32_t)(p1 - p0));
+        }
       }
       for (int j = tid; j < ncols * 8; j += T) {
         const int l = j >> 3, e = j & 7;
