@@ -435,6 +435,7 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
     uint16_t* ordB = S.ordB;
     int which = 0;
     int level = c.level;
+    int prev_global = 0;  // the previous level's cell table lives in the global slice
     for (;;) {
       const uint32_t ncur = s_ncur;
       if (ncur == 0) break;
@@ -444,6 +445,10 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
       auto level_body = [&](auto in_global) {
         LCell* cc = decltype(in_global)::value ? gslice + (size_t)which * slice_cells
                                                : S.tab + which * kCells;
+        // the previous level's table: its cells' mkey holds the numbers of
+        // their live children (kNoCell for a finished one), low half left
+        const LCell* cprev = prev_global ? gslice + (size_t)(which ^ 1) * slice_cells : S.tab + (which ^ 1) * kCells;
+        const bool first = level == (int)c.level;
 
         // ---- 1. key coordinate of every live cell
         if (t.key_rule == KEY_CYCLIC) {
@@ -546,6 +551,12 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
           bool f = false;
           if (i < N) {
             k = S.cellid[i];
+            if (!first && k != kNoCell) {
+              // the position's cell at this level: a child of its previous cell
+              const LCell& pc = cprev[k];
+              k = (pc.mkey >> ((i - pc.begin) >= pc.lcount ? 16u : 0u)) & 0xffffu;
+              S.cellid[i] = (uint16_t)k;
+            }
             if (k != kNoCell) {
               const uint32_t o = ordA[i];
               const uint32_t cb = cc[k].begin;
@@ -707,8 +718,8 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
         }
 
         // ---- 6. children: a scan over the cells numbers the live children
-        // (their number is parked in the parent's mkey); then every position
-        // takes its child's number
+        // (their number is parked in the parent's mkey); every position takes
+        // its child's number when the next level reads its cell (step 2)
         const int nlevel = level + 1;
         uint32_t run_out = 0;
         int nwhere = 0;
@@ -803,16 +814,10 @@ k_subtree(const TreeDev* trees, const Cell* list, uint32_t count, const uint32_t
           s_ncur = run_out;
           s_where = (uint32_t)nwhere;
         }
+        // every position takes its child's number at the start of the next
+        // level (from this table's mkey); the barrier publishes the table
         __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-          const uint32_t i = (uint32_t)tid + (uint32_t)q * T;
-          const uint32_t k = kq[q];
-          if (i >= N || k == kNoCell) continue;
-          const uint32_t side = (i - cc[k].begin) >= cc[k].lcount ? 16u : 0u;
-          S.cellid[i] = (uint16_t)(cc[k].mkey >> side);
-        }
-        __syncthreads();
+        prev_global = decltype(in_global)::value ? 1 : 0;
         which ^= 1;
         level = nlevel;
       };
