@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
   __shared__ SubMeta meta[2];
   __shared__ uint32_t wcnt[kMaxItems][kCW];
   __shared__ uint32_t sedge[kMaxItems][kCW];  // subset of each warp's last point per round
+  __shared__ unsigned wbal[kMaxItems][kCW];   // each (round, warp) block's left flags (explicit ids)
   __shared__ uint32_t tmm[2][kMaxDims][2];    // this CTA's run of tiles of one cell: per child,
                                               // min / max key per coordinate
   __shared__ uint32_t s_fail;
@@ -314,8 +315,12 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         if (lane == 0) wcnt[q][warp] = __popc(bal[q]);
         sv[q] = 0;
         if (want_off) {
-          if (i < mcnt) sv[q] = explicit_sid ? sid_of(i) : meta_subset(m, pa[i]);
-          if (lane == 31) sedge[q][warp] = sv[q];
+          if (explicit_sid) {
+            if (lane == 0) wbal[q][warp] = bal[q];
+          } else {
+            if (i < mcnt) sv[q] = meta_subset(m, pa[i]);
+            if (lane == 31) sedge[q][warp] = sv[q];
+          }
         }
       }
       named_sync(kConsumerBar, kCT);
@@ -446,7 +451,40 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       }
       // ---- subset offsets of the big children, at the segment starts
       // (each row holds r + 1 words below off_cap, checked when it was handed out)
-      if (want_off) {
+      if (want_off && explicit_sid) {
+        // thread tid checks positions 4 tid .. 4 tid + 3 against the one before
+        // each, reading the staged ids; only a warp holding a subset change or
+        // the cell's last point goes on, taking the left rank of a position
+        // from its block's count scan and left-flag ballot
+        const uint32_t r = m.r, i0 = 4u * (uint32_t)tid;
+        uint32_t v[5];
+        v[0] = i0 == 0u ? m.prev_sub : sid_of(i0 - 1u);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j + 1] = i0 + j < mcnt ? sid_of(i0 + j) : v[j];
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) any |= i0 + j < mcnt && (v[j] != v[j + 1] || m.sub + i0 + j + 1u == ccount);
+        if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint32_t i = i0 + j;
+            const uint32_t blk = ((i / kCT) * kCW + ((i % kCT) >> 5)) & 31u;  // i < kMaxItems kCT
+            const uint32_t lr = __shfl_sync(0xffffffffu, wexc, blk) +
+                                __popc((&wbal[0][0])[blk] & ((1u << (i & 31u)) - 1u));
+            if (i >= mcnt) continue;
+            const uint32_t p = m.sub + i, lk = lnext - cbeg + lr;  // left points of the cell before i
+            for (int32_t u = (int32_t)v[j] + 1; u <= (int32_t)v[j + 1]; ++u) {
+              if (m.row[0] != kNoRow) s.off_next[m.row[0] + u] = lk;
+              if (m.row[1] != kNoRow) s.off_next[m.row[1] + u] = p - lk;
+            }
+            if (p + 1 == ccount)
+              for (uint32_t u = v[j + 1] + 1; u <= r; ++u) {
+                if (m.row[0] != kNoRow) s.off_next[m.row[0] + u] = L;
+                if (m.row[1] != kNoRow) s.off_next[m.row[1] + u] = ccount - L;
+              }
+          }
+        }
+      } else if (want_off) {
         const uint32_t r = m.r;
 #pragma unroll
         for (int q = 0; q < kMaxItems; ++q) {
