@@ -60,7 +60,7 @@ struct SubMeta {
   int64_t n;
   uint32_t cell_begin, cell_count, cell_idx, tile, sub, mcnt, T, dim, mkey, L, loff, tile_start;
   uint32_t row[2];     // rows of the children's subset offsets (kNoRow: not a big child)
-  uint32_t prev_sub;   // subset of the point before the sub-tile (~0u at the cell's start)
+  uint32_t prev_sub;   // subset of the point before the CTA's first sub-tile (~0u at a cell's start)
   uint32_t r, subset_mode, sid_bytes, sid_ph, tn;
   int32_t d;
   uint8_t term_left, term_right, want_mm, want_off, level0;
@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
   __shared__ uint32_t tmm[2][kMaxDims][2];    // this CTA's run of tiles of one cell: per child,
                                               // min / max key per coordinate
   __shared__ uint32_t s_fail;
+  __shared__ uint32_t s_carry;  // subset of the last point of the sub-tile the consumers finished last
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ntiles = *s.ntiles_total;
   // this CTA's contiguous range of tiles: consecutive tiles mostly share a
@@ -237,11 +238,14 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         }
         if (!P)
           for (uint32_t i = lane; i < mcnt; i += 32) A[(size_t)d * stride + i] = g0 + i;
-        // the subset of the point before the sub-tile: a global load, read once
-        // the copies are on their way
+        // the subset of the point before the CTA's first sub-tile, if that is
+        // not a cell's start: one global load per CTA (each later sub-tile
+        // follows the one before it in the same cell, whose last subset the
+        // consumers keep)
         if (lane == 0)
-          m.prev_sub = (sub > 0u && (cr0.x != kNoRow || cr1.x != kNoRow)) ? subset_at(tg, c.level, (int64_t)g0 - 1)
-                                                                          : 0xffffffffu;
+          m.prev_sub = (k == 0 && sub > 0u && (cr0.x != kNoRow || cr1.x != kNoRow))
+                           ? subset_at(tg, c.level, (int64_t)g0 - 1)
+                           : 0xffffffffu;
         cp_async_mbar_arrive(&full[b]);  // this lane's edge copies count toward the phase
         __syncwarp();
         if (lane == 0) mbar_arrive(&full[b]);
@@ -290,6 +294,11 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       const bool term_left = m.term_left, term_right = m.term_right;
       const bool want_mm = m.want_mm, want_off = m.want_off, level0 = m.level0;
       const bool explicit_sid = m.sid_bytes != 0;
+      // subset of the point before this sub-tile (~0u at the cell's start):
+      // the CTA's sub-tiles run in position order, so after its first one it
+      // is the last subset of the previous sub-tile (read here, before this
+      // sub-tile's second consumer barrier; rewritten after it)
+      const uint32_t prev_sub = m.sub == 0u ? 0xffffffffu : (k == 0 ? m.prev_sub : s_carry);
       if (m.sub == m.tile_start) {
         lnext = cbeg + m.loff;
         rnext = cbeg + L + (m.tile_start - m.loff);
@@ -458,9 +467,10 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
         // from its block's count scan and left-flag ballot
         const uint32_t r = m.r, i0 = 4u * (uint32_t)tid;
         uint32_t v[5];
-        v[0] = i0 == 0u ? m.prev_sub : sid_of(i0 - 1u);
+        v[0] = i0 == 0u ? prev_sub : sid_of(i0 - 1u);
 #pragma unroll
         for (int j = 0; j < 4; ++j) v[j + 1] = i0 + j < mcnt ? sid_of(i0 + j) : v[j];
+        if (i0 < mcnt && i0 + 4u >= mcnt) s_carry = v[4];  // the sub-tile's last subset
         bool any = false;
 #pragma unroll
         for (int j = 0; j < 4; ++j) any |= i0 + j < mcnt && (v[j] != v[j + 1] || m.sub + i0 + j + 1u == ccount);
@@ -492,8 +502,9 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           const uint32_t p = m.sub + i;  // position in the cell
           int32_t sp = __shfl_up_sync(0xffffffffu, (int32_t)sv[q], 1);
           if (lane == 0)
-            sp = (int32_t)(warp > 0 ? sedge[q][warp - 1] : (q > 0 ? sedge[q - 1][kCW - 1] : m.prev_sub));
+            sp = (int32_t)(warp > 0 ? sedge[q][warp - 1] : (q > 0 ? sedge[q - 1][kCW - 1] : prev_sub));
           if (i >= mcnt) continue;
+          if (i + 1 == mcnt) s_carry = sv[q];
           if ((int32_t)sv[q] != sp)
             for (uint32_t u = (uint32_t)(sp + 1); u <= sv[q]; ++u) {
               if (m.row[0] != kNoRow) s.off_next[m.row[0] + u] = lrk[q];
