@@ -152,6 +152,25 @@ def measured_peak_gbs() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
+def copy_rates(host, dev) -> tuple:
+    """Pinned host <-> device copy rates (GB/s) of 1 GiB taken from `host`,
+    each the best of three."""
+    import torch
+    n = min(host.numel(), (1 << 30) // 4)
+    h = host.reshape(-1)[:n]
+    d = torch.empty(n, dtype=h.dtype, device=dev)
+    best = [float("inf"), float("inf")]
+    for _ in range(3):
+        for k, (dst, src) in enumerate(((d, h), (h, d))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            best[k] = min(best[k], time.perf_counter() - t0)
+    del d
+    return n * 4 / best[0] / 1e9, n * 4 / best[1] / 1e9
+
+
 def recorded_traffic(kernel: str, workload_name: str):
     """DRAM bytes per point of `kernel` from the committed ncu summary, if the
     kernel sources are unchanged since it was taken."""
@@ -543,6 +562,11 @@ def main() -> None:
                "h2d_bytes_per_step": spec.d * spec.n * 4 + spec.n * sid_bytes,
                "d2h_bytes_per_step": spec.n * 4 + (nleaf - 1) * 5 + (nleaf + 1) * 8,
                "ms_per_step": 1e3 * e_s / args.steps}
+        # this box's pinned copy rates (the copies alone bound the end-to-end time from below)
+        h2d, d2h = copy_rates(host_pts, dev)
+        e2e.update({"h2d_gbs": h2d, "d2h_gbs": d2h,
+                    "copies_ms": 1e3 * (e2e["h2d_bytes_per_step"] / (h2d * 1e9) +
+                                        e2e["d2h_bytes_per_step"] / (d2h * 1e9))})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
