@@ -37,7 +37,10 @@
  * on `stream` (a cudaStream_t; NULL = legacy default stream) and return after
  * the build has finished: the host waits on the stream while a build runs
  * (it reads the next level's cell counts between levels) and once at its end
- * (the status). No function allocates device memory except where stated.
+ * (the status). So no build or query may be issued on a stream that is being
+ * captured into a CUDA graph: such a call returns KDT_ERR_INVALID_ARG before
+ * it touches the stream. No function allocates device memory except where
+ * stated.
  */
 #ifndef KDT_H
 #define KDT_H
@@ -320,10 +323,10 @@ int32_t kdt_trace_read(kdt_kernel_stat *out, int32_t max, int32_t reset);
  *   exits. Problems whose kdt_workspace_size exceeds 64 MiB are rejected with
  *   KDT_ERR_CAPACITY (about one million 3-D points; fewer in higher d).
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture. Later calls reuse the address. Like
- *   kdt_build, every call waits on its stream while it runs (see the
- *   conventions at the top of this file).
+ *   (cudaGetSymbolAddress) with that device current; later calls reuse it.
+ *   Like kdt_build, every call waits on its stream while it runs, so none
+ *   may be issued during a stream capture (see the conventions at the top of
+ *   this file).
  *   All calls on a device share the array: calls that overlap on the GPU (for
  *   example on two streams) race and produce garbage. Issue them in order.
  *   Arguments, outputs and errors are those of kdt_build (without workspace).

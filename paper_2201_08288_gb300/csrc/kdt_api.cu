@@ -13,6 +13,7 @@
 #include "kdt.h"
 #include "kdt_engine.h"
 #include "kdt_launch.h"
+#include "kdt_trace.h"
 
 namespace kdt {
 namespace {
@@ -96,6 +97,7 @@ kdt_status kdt_build(const float* points, const kdt_params* p, void* workspace, 
                      int64_t* out_node_offsets, int32_t* out_levels, void* stream) {
   const kdt_status v = validate_params(p);
   if (v != KDT_OK) return v;
+  if (capturing((cudaStream_t)stream)) return KDT_ERR_INVALID_ARG;  // the build waits on its stream
   if ((p->n > 0 && (!points || !out_perm)) || !out_node_offsets) return KDT_ERR_INVALID_ARG;
   const int L_cap = p->depth > 0 ? p->depth : p->max_levels;
   if (L_cap > 0 && (!out_split_vals || !out_split_dims)) return KDT_ERR_INVALID_ARG;
@@ -141,6 +143,7 @@ kdt_status kdt_build_host(const float* points_host, const kdt_params* p, void* w
                           void* stream) {
   const kdt_status v = validate_params(p);
   if (v != KDT_OK) return v;
+  if (capturing((cudaStream_t)stream)) return KDT_ERR_INVALID_ARG;  // the build waits on its stream
   if ((p->n > 0 && (!points_host || !out_perm_host)) || !out_node_offsets_host) return KDT_ERR_INVALID_ARG;
   size_t need = 0;
   kdt_workspace_size_host(p, &need);

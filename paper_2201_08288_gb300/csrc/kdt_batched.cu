@@ -11,6 +11,7 @@
 
 #include "kdt.h"
 #include "kdt_engine.h"
+#include "kdt_trace.h"
 
 namespace {
 
@@ -64,6 +65,7 @@ kdt_status kdt_build_batched(const kdt_tree_desc* trees, int32_t num_trees, void
   BatchPlan bp;
   kdt_status s = plan_batch(trees, num_trees, &bp);
   if (s != KDT_OK) return s;
+  if (kdt::capturing((cudaStream_t)stream)) return KDT_ERR_INVALID_ARG;  // the build waits on its stream
   for (int32_t i = 0; i < num_trees; ++i) {
     const kdt_tree_desc& t = trees[i];
     const int L_cap = t.params.depth > 0 ? t.params.depth : t.params.max_levels;

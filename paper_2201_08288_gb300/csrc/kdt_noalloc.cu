@@ -12,6 +12,7 @@
 
 #include "kdt.h"
 #include "kdt_launch.h"
+#include "kdt_trace.h"
 
 namespace {
 
@@ -34,6 +35,7 @@ extern "C" kdt_status kdt_build_noalloc(const float* points, const kdt_params* p
   const kdt_status v = kdt_workspace_size(p, &need);
   if (v != KDT_OK) return v;
   if (need > kNoallocScratchBytes) return KDT_ERR_CAPACITY;  // problem too large for the fixed scratch
+  if (kdt::capturing((cudaStream_t)stream)) return KDT_ERR_INVALID_ARG;  // the build waits on its stream
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     (void)cudaGetLastError();

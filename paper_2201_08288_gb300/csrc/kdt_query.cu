@@ -214,6 +214,7 @@ kdt_status kdt_query_box(const float* points, int64_t n, int32_t d, const uint32
   const kdt_status v = check_tree(points, n, d, perm, split_vals, split_dims, node_offsets, levels);
   if (v != KDT_OK) return v;
   if (nq < 0 || (nq > 0 && (!lo || !hi || !out_count)) || (out_list && list_cap == 0)) return KDT_ERR_INVALID_ARG;
+  if (capturing((cudaStream_t)stream)) return KDT_ERR_INVALID_ARG;  // the query waits on its stream
   if (nq == 0) return KDT_OK;
   const TreeView tv{points, n, d, levels, perm, split_vals, split_dims, node_offsets};
   cudaStream_t st = (cudaStream_t)stream;
@@ -236,6 +237,7 @@ kdt_status kdt_query_knn(const float* points, int64_t n, int32_t d, const uint32
   if (v != KDT_OK) return v;
   if (nq < 0 || k < 1 || k > KDT_KNN_MAX_K || (nq > 0 && (!queries || !out_idx || !out_dist2)))
     return KDT_ERR_INVALID_ARG;
+  if (capturing((cudaStream_t)stream)) return KDT_ERR_INVALID_ARG;  // the query waits on its stream
   if (nq == 0) return KDT_OK;
   const TreeView tv{points, n, d, levels, perm, split_vals, split_dims, node_offsets};
   cudaStream_t st = (cudaStream_t)stream;

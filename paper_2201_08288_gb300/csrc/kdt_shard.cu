@@ -601,6 +601,7 @@ extern "C" kdt_status kdt_build_sharded(const float* points, const kdt_params* p
   if (p->depth < 1 || p->fourier_j != 0 || shards < 1 || shards > kdt::kMaxShards) return KDT_ERR_INVALID_ARG;
   if ((p->n > 0 && (!points || !out_perm)) || !out_node_offsets || !out_split_vals || !out_split_dims)
     return KDT_ERR_INVALID_ARG;
+  if (kdt::capturing((cudaStream_t)stream)) return KDT_ERR_INVALID_ARG;  // the build waits on its stream
   return kdt::sharded_build(points, *p, shards, out_perm, out_split_vals, out_split_dims, out_node_offsets,
                             out_levels, (cudaStream_t)stream);
 }

@@ -195,3 +195,38 @@ def test_server_cancels_queued_requests_only():
         else:
             assert st == 0
             assert_same_tree(_host_tree(t), oracle.build_tree(host[i][0], **host[i][1]), f"request {i}")
+
+
+def test_calls_on_a_capturing_stream_are_refused():
+    """A build or query waits on its stream, so one issued while the stream is
+    being captured into a CUDA graph is refused with an invalid-argument
+    status before it touches the stream: the capture stays valid and a later
+    build on the same stream is right."""
+    from paper_2201_08288_gb300 import kdt
+    dev = torch.device("cuda:0")
+    pts_np = workloads.uniform(5000, 3, seed=71)
+    pts = torch.from_numpy(pts_np).to(dev)
+    kw = dict(r=4, subset_mode=0, depth=6)
+    ws = torch.empty(kdt.kdt_workspace_size(kdt.make_params(5000, 3, **kw)), dtype=torch.uint8, device=dev)
+    outs = _outputs(5000, 6)
+    tree = kdt.kdt_build(pts, workspace=ws, outputs=_outputs(5000, 6), **kw)
+    lo = torch.zeros((3, 4), device=dev)
+    hi = torch.ones((3, 4), device=dev)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    calls = [lambda: kdt.kdt_build(pts, workspace=ws, outputs=outs, stream=s, **kw),
+             lambda: kdt.kdt_build_noalloc(pts, outputs=outs, stream=s, **kw),
+             lambda: kdt.kdt_query_box(pts, tree, lo, hi, stream=s)]
+    statuses = []
+    with torch.cuda.graph(g, stream=s):
+        for call in calls:
+            try:
+                call()
+                statuses.append(0)
+            except kdt.KdtError as e:
+                statuses.append(e.status)
+    assert statuses == [1, 1, 1]
+    again = kdt.kdt_build(pts, workspace=ws, outputs=outs, stream=s, **kw)
+    torch.cuda.synchronize()
+    assert_same_tree(_host_tree(again), oracle.build_tree(pts_np, **kw), "after a refused capture")
