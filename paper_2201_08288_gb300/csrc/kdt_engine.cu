@@ -150,6 +150,7 @@ void StepNeeds::add(const kdt_params& p0, const TreePlan& tp) {
   slice_cells = std::max<uint32_t>(slice_cells, (uint32_t)tp.small_max);
   widest = widest || p.key_rule == KDT_KEY_WIDEST_SPREAD;
   max_d = std::max(max_d, (int)p.d);
+  max_r = std::max(max_r, (int)p.r);
   min_d = std::min(min_d, (int)p.d);
 }
 
@@ -397,7 +398,7 @@ kdt_status Engine::tick() {
     s_.obase_cur = obase_[cur_];
     s_.off_next = off_[cur_ ^ 1];
     s_.obase_next = obase_[cur_ ^ 1];
-    const uint64_t nseg_bound = std::min<uint64_t>((uint64_t)big_count_ * KDT_MAX_SUBSETS, plan_.nseg_cap);
+    const uint64_t nseg_bound = std::min<uint64_t>((uint64_t)big_count_ * (uint64_t)plan_.needs.max_r, plan_.nseg_cap);
     // tiles of this step: at most one per kTile points plus one per cell (a
     // tight launch size; the plan's max_tiles is the capacity of a full forest)
     // (the point counter is one device word: trust it only while it cannot wrap)

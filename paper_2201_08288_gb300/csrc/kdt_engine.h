@@ -53,6 +53,7 @@ struct StepNeeds {
   bool widest = false;
   bool fourier = false;  // a tree splits by the Fourier-moment estimator
   int max_d = 1, min_d = 1 << 30;  // min_d == max_d: every tree has the same d
+  int max_r = 1;                   // the largest subset count: segments per cell
   void add(const kdt_params& p, const TreePlan& tp);
 };
 

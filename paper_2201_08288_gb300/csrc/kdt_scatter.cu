@@ -63,7 +63,7 @@ struct SubMeta {
   uint32_t prev_sub;   // subset of the point before the CTA's first sub-tile (~0u at a cell's start)
   uint32_t r, subset_mode, sid_bytes, sid_ph, tn;
   int32_t d;
-  uint8_t term_left, term_right, want_mm, want_off, level0;
+  uint8_t term_left, term_right, want_mm, want_off, nan_check;
   uint8_t run_more;  // this CTA's next tile is of the same cell (its min / max run goes on)
   uint8_t pad1, pad2;
   uint32_t ph[kMaxDims + 1];  // alignment phase of each staged word column
@@ -188,7 +188,9 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           m.term_right = term_right;
           m.want_mm = tg.key_rule == KEY_WIDEST && !(term_left && term_right);
           m.want_off = cr0.x != kNoRow || cr1.x != kNoRow;
-          m.level0 = c.level == 0;
+          // the input's NaN check: the root's first pass over its columns (a
+          // presorted root's presort checks them)
+          m.nan_check = c.level == 0 && !tg.presorted;
           m.run_more = run_more;
         }
         uint32_t total = expl ? (sa1 - sa0) * (uint32_t)es : 0u;
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
       const uint32_t cbeg = m.cell_begin, ccount = m.cell_count;
       const uint32_t tend = min(m.tile_start + (uint32_t)kTile, ccount);
       const bool term_left = m.term_left, term_right = m.term_right;
-      const bool want_mm = m.want_mm, want_off = m.want_off, level0 = m.level0;
+      const bool want_mm = m.want_mm, want_off = m.want_off, nan_check = m.nan_check;
       const bool explicit_sid = m.sid_bytes != 0;
       // subset of the point before this sub-tile (~0u at the cell's start):
       // the CTA's sub-tiles run in position order, so after its first one it
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(kST, 2) k_scatter_tma(const TreeDev* trees, St
           v0[q] = i < mcnt ? a0[i] : 0u;
           v1[q] = i < mcnt ? a1[i] : 0u;
         }
-        if (level0)
+        if (nan_check)
 #pragma unroll
           for (int q = 0; q < kMaxItems; ++q)
             saw_nan |= (tid + q * kCT < mcnt) &&

@@ -295,6 +295,9 @@ __global__ void __launch_bounds__(kPsThreads) k_ps_move(const TreeDev* trees, St
       v[q] = i < end ? __ldg(X + i) : 0u;
     }
   };
+  // the input's NaN check (the scatter of a presorted root skips it): a NaN
+  // key lies above +inf's or below -inf's
+  bool nan = false;
   load(0, x);
   for (int l = 0; l < t.d; ++l) {
     if (l + 1 < t.d) load(l + 1, xn);
@@ -307,18 +310,23 @@ __global__ void __launch_bounds__(kPsThreads) k_ps_move(const TreeDev* trees, St
           lo = min(lo, k);
           hi = max(hi, k);
         }
+      nan |= hi > 0xff800000u || lo < 0x007fffffu;
       lo = __reduce_min_sync(0xffffffffu, lo);
       hi = __reduce_max_sync(0xffffffffu, hi);
       if ((threadIdx.x & 31) == 0) {
         atomic_min_shared(&gmm[l][0], lo);
         atomic_max_shared(&gmm[l][1], hi);
       }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kPsItems; ++q) nan |= sub[q] != 0xffffffffu && is_nan_bits(__uint_as_float(x[q]));
     }
     uint32_t* out = (uint32_t*)(t.xbuf[1] + (int64_t)l * n);
     pass([&](int q) { return x[q]; }, [&](uint32_t dst, uint32_t v) { out[dst] = v; });
 #pragma unroll
     for (int q = 0; q < kPsItems; ++q) x[q] = xn[q];
   }
+  if (nan) set_status(t, ST_NAN_INPUT);
   if (want_mm)  // the passes' barriers order the shared-memory reductions before this
     for (int j = threadIdx.x; j < 2 * t.d; j += kPsThreads)
       s.tile_mm[((size_t)blockIdx.x * 2 * kMaxDims + j / 2) * 2 + (j & 1)] = gmm[j / 2][j & 1];
@@ -1439,8 +1447,11 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
     }
     if (max_bigseg) {
       TraceScope ts(K_SELECT_BIG, st);
-      const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>(max_bigseg, sms * 4u));
-      if (tune.cta_threads == 512) {
+      // nseg bounds the big segments too; with few of them (the first levels
+      // of a large tree) a CTA's loads in flight set the rate, so they take
+      // 512 threads whatever the tuning
+      const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>(std::min(max_bigseg, nseg), sms * 4u));
+      if (tune.cta_threads == 512 || nseg <= sms * 4u) {
         if (tune.digit_bits == 8)
           k_select_big<512, 8><<<grid, 512, 0, st>>>(trees, s);
         else
