@@ -26,12 +26,16 @@ def _gpu():
 
 def _cases():
     """Segments of every select path: config 3's recipe (r = 256 explicit,
-    widest; root segments of 4096 keys) and a cyclic r = 8 tree whose root
-    segments hold 2^17 keys."""
+    widest; root segments of 4096 keys), a cyclic r = 8 tree whose root
+    segments hold 2^17 keys, and a clustered one: uniform on [1, 2), where
+    every key shares its sign and exponent and the CTA select's first digit
+    leaves 2^15 keys in each of four bins."""
     s3 = workloads.config3(n=1 << 20, depth=13)
     pts1 = np.random.default_rng(21).standard_normal((3, 1 << 20)).astype(np.float32)
+    pts2 = (1.0 + np.random.default_rng(22).random((3, 1 << 18))).astype(np.float32)
     return [("c3", s3.points(), s3.sids(), dict(r=256, subset_mode=2, depth=13, key_rule=1)),
-            ("r8", pts1, None, dict(r=8, subset_mode=0, depth=12, key_rule=0))]
+            ("r8", pts1, None, dict(r=8, subset_mode=0, depth=12, key_rule=0)),
+            ("u12", pts2, None, dict(r=2, subset_mode=0, depth=6, key_rule=0))]
 
 
 def _tunings():
