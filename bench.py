@@ -550,8 +550,11 @@ def main() -> None:
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
+        calls = []  # each call ends with its stream synchronised: per-call host times
         for _ in range(args.steps):
+            tq = time.perf_counter()
             ht = e2e_once()
+            calls.append(time.perf_counter() - tq)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -561,7 +564,10 @@ def main() -> None:
         e2e = {"value": world * args.steps * spec.n * ht.levels / e_s, "unit": UNIT,
                "h2d_bytes_per_step": spec.d * spec.n * 4 + spec.n * sid_bytes,
                "d2h_bytes_per_step": spec.n * 4 + (nleaf - 1) * 5 + (nleaf + 1) * 8,
-               "ms_per_step": 1e3 * e_s / args.steps}
+               "ms_per_step": 1e3 * e_s / args.steps,
+               # the spread of single calls (this rank): a slow copy shows as one outlier
+               "call_ms": {"min": 1e3 * min(calls), "median": 1e3 * statistics.median(calls),
+                           "max": 1e3 * max(calls)}}
         # this box's pinned copy rates (the copies alone bound the end-to-end time from below)
         h2d, d2h = copy_rates(host_pts, dev)
         e2e.update({"h2d_gbs": h2d, "d2h_gbs": d2h,
