@@ -51,30 +51,47 @@ __device__ __forceinline__ bool tile_of(const StepDev& s, uint32_t tile, uint2* 
 // ---------------------------------------------------------------- prep
 
 // Single CTA: per-cell tile and segment counts, exclusive scans, key dims
-// that are already known.
+// that are already known. Each thread takes kPrepItems consecutive cells per
+// round, so a deep level's many cells cost few block scans.
+constexpr int kPrepItems = 4;
+
 __global__ void k_prep(const TreeDev* trees, StepDev s) {
   __shared__ uint32_t tmp[33];
   uint32_t tile_run = 0, seg_run = 0;
   const uint32_t ncells = ncells_of(s);
-  for (uint32_t c0 = 0; c0 < ncells; c0 += blockDim.x) {
-    const uint32_t c = c0 + threadIdx.x;
-    uint32_t nt = 0, ns = 0;
-    if (c < ncells) {
-      const Cell cell = s.cells[c];
-      const TreeDev& t = trees[cell.tree];
-      nt = (cell.count + kTile - 1) / kTile;
-      ns = (uint32_t)t.r;
-      if (t.key_rule == KEY_CYCLIC)
-        s.kdim[c] = (uint32_t)(cell.level % t.d);
-      else if (cell.dim >= 0)
-        s.kdim[c] = (uint32_t)cell.dim;
+  for (uint32_t c0 = 0; c0 < ncells; c0 += blockDim.x * kPrepItems) {
+    const uint32_t cb = c0 + threadIdx.x * kPrepItems;
+    uint32_t nt[kPrepItems], ns[kPrepItems], st = 0, ss = 0;
+#pragma unroll
+    for (int q = 0; q < kPrepItems; ++q) {
+      const uint32_t c = cb + q;
+      nt[q] = 0;
+      ns[q] = 0;
+      if (c < ncells) {
+        const Cell cell = s.cells[c];
+        const TreeDev& t = trees[cell.tree];
+        nt[q] = (cell.count + kTile - 1) / kTile;
+        ns[q] = (uint32_t)t.r;
+        if (t.key_rule == KEY_CYCLIC)
+          s.kdim[c] = (uint32_t)(cell.level % t.d);
+        else if (cell.dim >= 0)
+          s.kdim[c] = (uint32_t)cell.dim;
+      }
+      st += nt[q];
+      ss += ns[q];
     }
     uint32_t tot_t, tot_s;
-    const uint32_t et = block_excl_scan(nt, tmp, &tot_t);
-    const uint32_t es = block_excl_scan(ns, tmp, &tot_s);
-    if (c < ncells) {
-      s.tile_base[c] = tile_run + et;
-      s.seg_base[c] = seg_run + es;
+    uint32_t et = block_excl_scan(st, tmp, &tot_t);
+    uint32_t es = block_excl_scan(ss, tmp, &tot_s);
+#pragma unroll
+    for (int q = 0; q < kPrepItems; ++q) {
+      const uint32_t c = cb + q;
+      if (c < ncells) {
+        s.tile_base[c] = tile_run + et;
+        s.seg_base[c] = seg_run + es;
+      }
+      et += nt[q];
+      es += ns[q];
     }
     tile_run += tot_t;
     seg_run += tot_s;
@@ -572,7 +589,7 @@ __device__ __forceinline__ uint32_t thread_lower_median(const uint32_t* keys, ui
 // One thread per segment of at most tiny_max <= kSelTinyMax points (the
 // threads stride over the segments of the step). The network's size is
 // chosen per warp, by the warp's largest segment, so a warp never runs two.
-__global__ void __launch_bounds__(256) k_select_tiny(const TreeDev* trees, StepDev s) {
+__global__ void __launch_bounds__(256, 4) k_select_tiny(const TreeDev* trees, StepDev s) {
   const uint32_t nseg = s.seg_base[ncells_of(s)];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t stride = gridDim.x * blockDim.x;
