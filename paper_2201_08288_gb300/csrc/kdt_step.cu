@@ -589,7 +589,7 @@ __device__ __forceinline__ uint32_t thread_lower_median(const uint32_t* keys, ui
 // One thread per segment of at most tiny_max <= kSelTinyMax points (the
 // threads stride over the segments of the step). The network's size is
 // chosen per warp, by the warp's largest segment, so a warp never runs two.
-__global__ void __launch_bounds__(256, 4) k_select_tiny(const TreeDev* trees, StepDev s) {
+__global__ void __launch_bounds__(256, 5) k_select_tiny(const TreeDev* trees, StepDev s) {
   const uint32_t nseg = s.seg_base[ncells_of(s)];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t stride = gridDim.x * blockDim.x;
