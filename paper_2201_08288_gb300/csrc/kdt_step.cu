@@ -1241,7 +1241,7 @@ __device__ __forceinline__ void part_count_tile(const TreeDev* trees, const Step
 }
 
 // Warps stride over the tiles.
-__global__ void __launch_bounds__(256) k_part_count(const TreeDev* trees, StepDev s) {
+__global__ void __launch_bounds__(256, 3) k_part_count(const TreeDev* trees, StepDev s) {
   const uint32_t ntiles = *s.ntiles_total;
   for (uint32_t tile = blockIdx.x * 8u + (threadIdx.x >> 5); tile < ntiles; tile += gridDim.x * 8u)
     part_count_tile(trees, s, tile, s.tiles[tile]);
