@@ -165,7 +165,7 @@ __device__ void block_sort_slice(uint32_t* a, uint32_t m, int digits, LsShared& 
 
 // Grid (chunks, trees). Warps sort the small terminal cells, CTAs the middle
 // ones; the largest are listed for the global passes.
-__global__ void __launch_bounds__(kLsThreads) k_leaf_sort(const TreeDev* trees, const uint32_t* slots,
+__global__ void __launch_bounds__(kLsThreads, 4) k_leaf_sort(const TreeDev* trees, const uint32_t* slots,
                                                           uint32_t nslots) {
   __shared__ LsShared S;
   const uint32_t si = blockIdx.y;
