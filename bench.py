@@ -107,6 +107,11 @@ class Clocks:
         self.path = os.path.join(out_dir, f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
+        """Start sampling and wait (at most 10 s) for the first sample: the
+        sampler's own start-up (NVML initialisation, which on a fresh box takes
+        long enough to delay the build's host thread) stays out of the timed
+        region, which the caller opens later with mark()."""
+        self.offset = 0
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
@@ -115,6 +120,19 @@ class Clocks:
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 10.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
+
+    def mark(self):
+        """The timed region starts: stop() summarises the samples from here on."""
+        try:
+            self.offset = os.path.getsize(self.path)
+        except OSError:
+            self.offset = 0
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -127,7 +145,12 @@ class Clocks:
         self.fh.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as fh:
+            text = fh.read()
+        lines = text[self.offset:].splitlines()
+        if not any(len(x.split(",")) >= 9 for x in lines):  # a region shorter than one sample period
+            lines = text.splitlines()
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -269,13 +292,14 @@ def run_batched(args, dev, kdt) -> dict:
     descs, outs = kdt.make_descs(items)
     ws = torch.empty(kdt.kdt_workspace_size_batched(descs), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
     for _ in range(args.warmup):
         trees, st = kdt.kdt_build_batched(items, workspace=ws, outputs=outs, descs=descs, stream=stream)
     torch.cuda.synchronize()
     assert all(x == 0 for x in st), st
     units = sum(int(s.n) * t.levels for s, t in zip(specs, trees))
-    clocks = Clocks(dev.index or 0)
-    clocks.start()
+    clocks.mark()
     launches0 = kdt.kdt_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -469,16 +493,17 @@ def main() -> None:
                                          **{k: kw[k] for k in ("r", "subset_mode", "depth", "key_rule")})
         return kdt.kdt_build(pts, sid=sid, workspace=ws, outputs=out, stream=stream, **kw)
 
+    clocks = Clocks(dev.index if dev.index is not None else 0)
+    clocks.start()
     for _ in range(args.warmup):
         tree = build_once()
     torch.cuda.synchronize()
     levels = tree.levels
 
-    clocks = Clocks(dev.index if dev.index is not None else 0)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark()
     launches0 = kdt.kdt_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
