@@ -186,6 +186,25 @@ def test_nan_input_is_reported():
         assert e.value.status == 2
 
 
+# Every place the input is checked for NaN: the presort of a root in subset
+# order (by its per-column min / max keys under widest spread, value by value
+# otherwise), and the first pipeline pass of a root that is not presorted
+# (contiguous subsets). Quiet and signalling patterns of both signs, in a
+# coordinate that is not the first key.
+@pytest.mark.parametrize("mode,key_rule", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (2, 1)])
+@pytest.mark.parametrize("bits", [0x7FC00000, 0xFFC00000, 0x7F800001, 0xFF800001])
+def test_nan_input_is_reported_on_every_root_path(mode, key_rule, bits):
+    from paper_2201_08288_gb300 import kdt
+    n, d, r = 60000, 4, 16
+    rng = np.random.default_rng(7)
+    pts = rng.random((d, n), dtype=np.float32)
+    pts.view(np.uint32)[2, 12345] = np.uint32(bits)
+    sid = rng.integers(0, r, n).astype(np.uint8) if mode == 2 else None
+    with pytest.raises(kdt.KdtError) as e:
+        gpu_build(pts, sid=sid, r=r, subset_mode=mode, depth=6, key_rule=key_rule)
+    assert e.value.status == 2
+
+
 def test_level_cap_is_reported():
     from paper_2201_08288_gb300 import kdt
     pts = np.random.default_rng(2).random((2, 5000), dtype=np.float32)
