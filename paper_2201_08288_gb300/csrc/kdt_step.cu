@@ -105,25 +105,24 @@ __global__ void k_prep(const TreeDev* trees, StepDev s) {
   }
 }
 
-// One CTA per cell: tile list entries; zeroed subset counts of a presorted root.
+// One warp per cell: tile list entries; zeroed subset counts of a presorted
+// root. (Most cells of a deep level have one to three tiles.)
 __device__ __forceinline__ void tiles_cell(const TreeDev* trees, const StepDev& s, uint32_t c) {
+  const uint32_t lane = threadIdx.x & 31u;
   const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
-  for (uint32_t j = tb + threadIdx.x; j < te; j += blockDim.x)
-    s.tiles[j] = make_uint2(c, (j - tb) * (uint32_t)kTile);
+  for (uint32_t j = tb + lane; j < te; j += 32u) s.tiles[j] = make_uint2(c, (j - tb) * (uint32_t)kTile);
   const Cell cell = s.cells[c];
   if (cell.level == 0) {
     const TreeDev& t = trees[cell.tree];
     if (t.presorted)
-      for (int j = threadIdx.x; j < t.r; j += blockDim.x) t.root_cur[j] = 0;
+      for (uint32_t j = lane; j < (uint32_t)t.r; j += 32u) t.root_cur[j] = 0;
   }
 }
 
 __global__ void k_tiles(const TreeDev* trees, StepDev s) {
   const uint32_t nc = ncells_of(s);
-  for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
-    tiles_cell(trees, s, c);
-    __syncthreads();  // the cell's shared memory is free for the next one
-  }
+  const uint32_t wpb = blockDim.x >> 5;
+  for (uint32_t c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nc; c += gridDim.x * wpb) tiles_cell(trees, s, c);
 }
 
 // ------------------------------------------------------ root presort
@@ -1295,7 +1294,11 @@ __global__ void __launch_bounds__(256) k_part_scan_warp(StepDev s) {
 // and of each child queued for the subtree kernel (its first level), from its
 // min and max key per coordinate (reduced by the scatter): the
 // largest range (double)max - (double)min, 0 for equal keys, lowest
-// coordinate on ties.
+// coordinate on ties. A range is never negative, so the bit patterns of two
+// ranges order like the ranges as unsigned integers: the argmax runs on the
+// high word, then the low word, then the lowest coordinate, by integer warp
+// reductions (double arithmetic, slow on this part, only for the one
+// subtraction per range).
 __device__ __forceinline__ void child_dims_cell(const TreeDev* trees, const StepDev& s, uint32_t c) {
   const int lane = threadIdx.x & 31;
   const Cell cell = s.cells[c];
@@ -1305,25 +1308,20 @@ __device__ __forceinline__ void child_dims_cell(const TreeDev* trees, const Step
   for (int side = 0; side < 2; ++side) {
     const uint2 cr = s.crow[2 * c + side];
     if (cr.x == kNoRow && cr.y == kNoRow) continue;  // terminal
-    double rb = -1.0;
-    int ib = 0;
-    for (int l = lane; l < d; l += 32) {
+    uint64_t rb = 0ull;
+    uint32_t ib = 0xffffffffu;
+    for (int l = lane; l < d; l += 32) {  // l ascending: the first of equal ranges is kept
       const uint2 mm = *(const uint2*)&s.child_mm[(((size_t)c * 2 + side) * kMaxDims + l) * 2];
-      const double range = key_range(mm.x, mm.y);
-      if (range > rb) {
+      const uint64_t range = (uint64_t)__double_as_longlong(key_range(mm.x, mm.y));
+      if (ib == 0xffffffffu || range > rb) {
         rb = range;
-        ib = l;
+        ib = (uint32_t)l;
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double orb = __shfl_xor_sync(0xffffffffu, rb, o);
-      const int oib = __shfl_xor_sync(0xffffffffu, ib, o);
-      if (orb > rb || (orb == rb && oib < ib)) {
-        rb = orb;
-        ib = oib;
-      }
-    }
+    const uint32_t rh = (uint32_t)(rb >> 32), rl = (uint32_t)rb;
+    const uint32_t mh = __reduce_max_sync(0xffffffffu, ib != 0xffffffffu ? rh : 0u);
+    const uint32_t ml = __reduce_max_sync(0xffffffffu, (ib != 0xffffffffu && rh == mh) ? rl : 0u);
+    ib = __reduce_min_sync(0xffffffffu, (ib != 0xffffffffu && rh == mh && rl == ml) ? ib : 0xffffffffu);
     if (lane == 0) {
       if (cr.x != kNoRow)
         s.next_big[cr.x].dim = (int16_t)ib;
@@ -1427,7 +1425,7 @@ void launch_big_step(const TreeDev* trees, const StepDev& s, uint32_t max_tiles,
     return std::max<uint32_t>(1, dev ? std::min(g, cap) : g);
   };
   { TraceScope ts(K_PREP, st); k_prep<<<1, 1024, 0, st>>>(trees, s); }
-  { TraceScope ts(K_TILES, st); k_tiles<<<cells_grid(1, sms * 8u), 256, 0, st>>>(trees, s); }
+  { TraceScope ts(K_TILES, st); k_tiles<<<cells_grid(8, sms * 8u), 256, 0, st>>>(trees, s); }
   if (s.shards) launch_shard_index(s, nc, st);
   if (has_roots) {
     {
