@@ -106,7 +106,9 @@ __global__ void k_prep(const TreeDev* trees, StepDev s) {
 }
 
 // One warp per cell: tile list entries; zeroed subset counts of a presorted
-// root. (Most cells of a deep level have one to three tiles.)
+// root, and (widest spread, coordinate not known yet) the identities in its
+// first tile's min / max record, which the presort's groups reduce into.
+// (Most cells of a deep level have one to three tiles.)
 __device__ __forceinline__ void tiles_cell(const TreeDev* trees, const StepDev& s, uint32_t c) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t tb = s.tile_base[c], te = s.tile_base[c + 1];
@@ -114,8 +116,12 @@ __device__ __forceinline__ void tiles_cell(const TreeDev* trees, const StepDev& 
   const Cell cell = s.cells[c];
   if (cell.level == 0) {
     const TreeDev& t = trees[cell.tree];
-    if (t.presorted)
+    if (t.presorted) {
       for (uint32_t j = lane; j < (uint32_t)t.r; j += 32u) t.root_cur[j] = 0;
+      if (t.key_rule == KEY_WIDEST && cell.dim < 0 && tb < te)
+        for (uint32_t j = lane; j < 2u * (uint32_t)t.d; j += 32u)
+          s.tile_mm[((size_t)tb * 2 * kMaxDims + j / 2) * 2 + (j & 1)] = (j & 1) ? 0u : 0xffffffffu;
+    }
   }
 }
 
@@ -234,8 +240,9 @@ __global__ void __launch_bounds__(kPsThreads) k_ps_move(const TreeDev* trees, St
   Cell cell;
   if (!presort_tile(trees, s, blockIdx.x, &tl, &cell)) return;
   const TreeDev& t = trees[cell.tree];
-  // widest spread: the group's min / max key per coordinate go to the record
-  // of its first tile, the other tiles' records hold the identities
+  // widest spread: the group's min / max key per coordinate go by atomics into
+  // the record of the root's first tile, the other tiles' records hold the
+  // identities
   const bool want_mm = t.key_rule == KEY_WIDEST && cell.dim < 0;
   if ((tl.y / (uint32_t)kTile) % (uint32_t)kPsGroup != 0u) {  // the group's first tile runs it
     if (want_mm)
@@ -343,9 +350,17 @@ __global__ void __launch_bounds__(kPsThreads) k_ps_move(const TreeDev* trees, St
     for (int q = 0; q < kPsItems; ++q) x[q] = xn[q];
   }
   if (nan) set_status(t, ST_NAN_INPUT);
-  if (want_mm)  // the passes' barriers order the shared-memory reductions before this
-    for (int j = threadIdx.x; j < 2 * t.d; j += kPsThreads)
-      s.tile_mm[((size_t)blockIdx.x * 2 * kMaxDims + j / 2) * 2 + (j & 1)] = gmm[j / 2][j & 1];
+  if (want_mm) {  // the passes' barriers order the shared-memory reductions before this
+    // into the root's first tile record (identities set by k_tiles); this
+    // tile's own record, if another, holds the identities
+    const uint32_t tb = s.tile_base[tl.x];
+    for (int j = threadIdx.x; j < 2 * t.d; j += kPsThreads) {
+      uint32_t* acc = &s.tile_mm[((size_t)tb * 2 * kMaxDims + j / 2) * 2 + (j & 1)];
+      if (j & 1) atomicMax(acc, gmm[j / 2][1]); else atomicMin(acc, gmm[j / 2][0]);
+      if (blockIdx.x != tb)
+        s.tile_mm[((size_t)blockIdx.x * 2 * kMaxDims + j / 2) * 2 + (j & 1)] = (j & 1) ? 0u : 0xffffffffu;
+    }
+  }
   pass([&](int q) { return i0 + threadIdx.x + q * kPsThreads; },
        [&](uint32_t dst, uint32_t v) { t.pbuf[1][dst] = v; });
   if (expl) {
@@ -433,7 +448,10 @@ __device__ __forceinline__ void pick_dim_cell(const TreeDev* trees, const StepDe
   __syncthreads();
   // the roots of a sharded build's shards are parts of one root: every one
   // of them reduces the tiles of all
-  const uint32_t tb = s.shards ? 0u : s.tile_base[c], te = s.shards ? s.tile_base[ncells_of(s)] : s.tile_base[c + 1];
+  const uint32_t tb = s.shards ? 0u : s.tile_base[c];
+  // a presorted root's presort gathered its min / max in its first tile's
+  // record; other roots' are spread over their tiles
+  const uint32_t te = s.shards ? s.tile_base[ncells_of(s)] : (t.presorted ? tb + 1u : s.tile_base[c + 1]);
   const int lane = threadIdx.x & 31;
   for (int c0 = 0; c0 < t.d; c0 += 8) {
     const int nc = min(8, t.d - c0);
