@@ -164,7 +164,9 @@ __device__ void block_sort_slice(uint32_t* a, uint32_t m, int digits, LsShared& 
 }
 
 // Grid (chunks, trees). Warps sort the small terminal cells, CTAs the middle
-// ones; the largest are listed for the global passes.
+// ones; the largest are listed for the global passes. Four CTAs per SM by a
+// register bound: the warps' networks, which sort nearly every leaf of a deep
+// tree, want the warps; the CTA path spills a few words.
 __global__ void __launch_bounds__(kLsThreads, 4) k_leaf_sort(const TreeDev* trees, const uint32_t* slots,
                                                           uint32_t nslots) {
   __shared__ LsShared S;

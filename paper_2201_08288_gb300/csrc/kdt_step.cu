@@ -606,6 +606,9 @@ __device__ __forceinline__ uint32_t thread_lower_median(const uint32_t* keys, ui
 // One thread per segment of at most tiny_max <= kSelTinyMax points (the
 // threads stride over the segments of the step). The network's size is
 // chosen per warp, by the warp's largest segment, so a warp never runs two.
+// Five CTAs per SM by a register bound: the path waits on its loads, and more
+// warps hide that better than the 64-key network's registers (which then
+// spill a little) are worth.
 __global__ void __launch_bounds__(256, 5) k_select_tiny(const TreeDev* trees, StepDev s) {
   const uint32_t nseg = s.seg_base[ncells_of(s)];
   const uint32_t lane = threadIdx.x & 31u;
@@ -1257,7 +1260,8 @@ __device__ __forceinline__ void part_count_tile(const TreeDev* trees, const Step
   if (lane == 0) s.tile_left[tile] = cnt;
 }
 
-// Warps stride over the tiles.
+// Warps stride over the tiles; three CTAs per SM by a register bound (a
+// warp's sixteen 16-byte loads per lane still fit without spilling).
 __global__ void __launch_bounds__(256, 3) k_part_count(const TreeDev* trees, StepDev s) {
   const uint32_t ntiles = *s.ntiles_total;
   for (uint32_t tile = blockIdx.x * 8u + (threadIdx.x >> 5); tile < ntiles; tile += gridDim.x * 8u)
