@@ -1260,8 +1260,9 @@ __device__ __forceinline__ void part_count_tile(const TreeDev* trees, const Step
   if (lane == 0) s.tile_left[tile] = cnt;
 }
 
-// Warps stride over the tiles; three CTAs per SM by a register bound (a
-// warp's sixteen 16-byte loads per lane still fit without spilling).
+// Warps stride over the tiles; three CTAs per SM by a register bound (80
+// registers: a lane's sixteen 16-byte loads still fit, with a few words of
+// spill).
 __global__ void __launch_bounds__(256, 3) k_part_count(const TreeDev* trees, StepDev s) {
   const uint32_t ntiles = *s.ntiles_total;
   for (uint32_t tile = blockIdx.x * 8u + (threadIdx.x >> 5); tile < ntiles; tile += gridDim.x * 8u)
