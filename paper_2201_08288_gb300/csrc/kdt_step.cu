@@ -606,9 +606,10 @@ __device__ __forceinline__ uint32_t thread_lower_median(const uint32_t* keys, ui
 // One thread per segment of at most tiny_max <= kSelTinyMax points (the
 // threads stride over the segments of the step). The network's size is
 // chosen per warp, by the warp's largest segment, so a warp never runs two.
-// Five CTAs per SM by a register bound: the path waits on its loads, and more
-// warps hide that better than the 64-key network's registers (which then
-// spill a little) are worth.
+// Five CTAs per SM by a register bound (48 registers): the path waits on its
+// loads, and the extra warps hide that better than keeping the larger
+// networks in registers does (they spill about 300 bytes per thread to local
+// memory; measured faster than four or six CTAs per SM).
 __global__ void __launch_bounds__(256, 5) k_select_tiny(const TreeDev* trees, StepDev s) {
   const uint32_t nseg = s.seg_base[ncells_of(s)];
   const uint32_t lane = threadIdx.x & 31u;
